@@ -1,0 +1,77 @@
+"""Mutation check of the oracle's pins.
+
+Each case compiles a copy of oracle/fmm_oracle.c with one plausible mistake
+planted (a wrong sign, a dropped term, a wrong index or operand) and runs the
+pins of test_oracle_pins.py against it; at least one pin must fail.  The
+mistakes are planted only in throw-away copies of the oracle, on the CPU.
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_spec = importlib.util.spec_from_file_location(
+    "oracle_pins", os.path.join(_HERE, "test_oracle_pins.py"))
+pins = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(pins)
+
+MUTANTS = {
+    "discriminant_sign": ("double disc = qb * qb - (4.0 * qa) * qc;",
+                          "double disc = qb * qb + (4.0 * qa) * qc;"),
+    "dropped_z_term": ("((w2 * psi[2]) * psi[2])) - Finv2;", "0.0) - Finv2;"),
+    "wrong_axis_neighbour": ("else if (fabs(m->T[qp]) < fabs(m->T[qm]))",
+                             "else if (fabs(m->T[qp]) > fabs(m->T[qm]))"),
+    "missing_causality_axis": ("if (psi[0] < t && psi[1] < t && psi[2] < t) {",
+                               "if (psi[0] < t && psi[1] < t) {"),
+    "drops_smallest_axis": ("if (hh[a] != 0.0 && (j < 0 || psi[a] >= psi[j]))",
+                            "if (hh[a] != 0.0 && (j < 0 || psi[a] <= psi[j]))"),
+    "h_power": ("hh[a] = 1.0 / m->h;", "hh[a] = 1.0 / (m->h * m->h);"),
+    "speed_power": ("double Finv2 = 1.0 / (F * F);", "double Finv2 = 1.0 / F;"),
+    "crossing_fraction": ("double theta = fc / (fc - fq);",
+                          "double theta = fq / (fq - fc);"),
+    "fix_cells_updated": ("if (m->G[l] == ORC_KNOWN_FIX || !(fabs(m->T[l]) > Ti))",
+                          "if (!(fabs(m->T[l]) > Ti))"),
+    "adjoint_slowness_factor": ("dLds[p] = lam[p] * sp / D;",
+                                "dLds[p] = lam[p] / (sp * D);"),
+    "adjoint_dropped_weight": ("lam[nbr[q]] += lam[p] * (Tp - fabs(T[nbr[q]])) * w / D;",
+                               "lam[nbr[q]] += lam[p] * w / D;"),
+    "tangent_sign": ("dT[p] = (sp * v[p] + acc) / D;", "dT[p] = (sp * v[p] - acc) / D;"),
+}
+
+PINS = [
+    (pins.test_closed_forms_unit_speed, {}),
+    (pins.test_closed_forms_scaled, {}),
+    (pins.test_local_solve_cases, {}),
+    (pins.test_residual_and_fast_sweep_sources, {"seed": 2, "shape": (9, 13, 7)}),
+    (pins.test_two_sided_reinit, {"seed": 5, "shape": (12, 12, 12)}),
+    (pins.test_oblique_plane_front_exact, {"normal": (1.0, 1.0, 1.0)}),
+    (pins.test_axis_plane_exact, {}),
+    (pins.test_adjoint_finite_differences, {}),
+    (pins.test_adjoint_tangent_dot_product, {}),
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_rejected(oracle, tmp_path, name):
+    old, new = MUTANTS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    lib = oracle.compile_source(src.replace(old, new), str(tmp_path / f"lib_{name}.so"))
+    failed = []
+    with oracle.use_library(lib):
+        for fn, kw in PINS:
+            try:
+                with np.errstate(all="ignore"):
+                    fn(oracle, **kw)
+            except (AssertionError, ValueError, FloatingPointError, OverflowError):
+                failed.append(fn.__name__)
+    assert failed, f"no pin rejects the planted mistake {name}"
+
+
+def test_unmutated_copy_passes(oracle, tmp_path):
+    lib = oracle.compile_source(oracle.source_text(), str(tmp_path / "lib_copy.so"))
+    with oracle.use_library(lib):
+        for fn, kw in PINS:
+            fn(oracle, **kw)

@@ -1,0 +1,158 @@
+/*
+ * fmm.h -- C ABI of the GB300 restarted narrow band fast marching library
+ * (libfmm_gb300.so, CUDA for sm_103a).
+ *
+ * The library solves the Eikonal equation |grad psi| F = 1 (Eq. (1) of Yang &
+ * Stern, "A highly scalable massively parallel fast marching method for the
+ * Eikonal equation") on a uniform cell-centred 3-D grid with the first-order
+ * Godunov upwind scheme of Eq. (2)-(3), by the restarted narrow band method
+ * of Algorithm 16: subdomains (here 8x8x8 bricks of the grid) march locally up
+ * to a global bound that rises by a stride at every restart, exchange changed
+ * overlap data, and a global reduction of the front minimum sets the next
+ * bound and decides termination.
+ *
+ * Conventions shared by every entry point
+ *   - Grid arrays are nx*ny*nz elements, x fastest: idx = (k*ny + j)*nx + i,
+ *     psi at cell centres, spacing h on every axis (Sec. 2.1).  Cells outside
+ *     the grid do not exist; stencils never leave it (Sec. 4.1).
+ *   - Array arguments marked "device" are caller-owned device memory on the
+ *     current CUDA device, contiguous, 16-byte aligned, of the handle's dtype
+ *     (float for FMM_F32, double for FMM_F64) unless stated otherwise.  The
+ *     library never frees them and keeps no reference after the call returns.
+ *   - Work is enqueued on cfg->stream (NULL = the legacy default stream).
+ *     Entry points that run a solve return after it has finished (the restart
+ *     loop reads the device's termination flag), so outputs are ready when
+ *     they return FMM_OK.
+ *   - On any error the call returns a non-zero fmm_status, leaves the outputs
+ *     unspecified and records a message for fmm_last_error().
+ *   - A handle may be used by one host thread at a time.
+ *
+ * Output tags (uint8, when requested): 0 FAR (never reached, psi = +inf),
+ * 1 BAND (tentative value beyond width_band), 2 KNOWN (accepted),
+ * 3 FIX (an initial interface / source cell, KNOWN_FIX of Sec. 4.2).
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID = 1,   /* bad argument (sizes, pointers, speed <= 0, NaN) */
+    FMM_ERR_OOM = 2,       /* device allocation failed                        */
+    FMM_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
+    FMM_ERR_TIMEOUT = 4,   /* an iteration or restart limit was reached       */
+    FMM_ERR_STATE = 5      /* call order violated (e.g. adjoint before solve) */
+} fmm_status;
+
+typedef enum { FMM_F32 = 0, FMM_F64 = 1 } fmm_dtype;
+
+typedef enum { FMM_TAG_FAR = 0, FMM_TAG_BAND = 1, FMM_TAG_KNOWN = 2, FMM_TAG_FIX = 3 } fmm_tag;
+
+/* Solver configuration.  Zero-initialise and set nx, ny, nz, h, dtype; every
+ * other field has a default when left 0. */
+typedef struct {
+    int64_t nx, ny, nz;    /* grid size, each >= 1                              */
+    double h;              /* grid spacing (> 0)                                */
+    int32_t dtype;         /* fmm_dtype                                         */
+    int32_t record_tape;   /* 1: keep the upwind sets for fmm_adjoint           */
+    double width;          /* width_band (Algorithm 5/12); 0 -> +inf (full march) */
+    double stride;         /* restart stride delta_s in units of h (Algorithm 16);
+                              0 -> 2 (the paper's suggestion, Sec. 5.5);
+                              +inf allowed                                     */
+    double bucket;         /* accepted bucket width inside a brick, in units of
+                              h * min(1/F) / sqrt(3); 0 -> 1; +inf allowed     */
+    int32_t ctas;          /* CTAs of the march kernel; 0 -> as many as fit     */
+    int32_t timeout_s;     /* host wall-clock limit of one solve in seconds;
+                              0 -> 600; exceeding it returns FMM_ERR_TIMEOUT  */
+    int64_t max_restarts;  /* 0 -> no limit other than the grid's size          */
+    void *stream;          /* cudaStream_t                                      */
+} fmm_config;
+
+/* Statistics of the last solve on a handle. */
+typedef struct {
+    int64_t restarts;        /* passes of the Algorithm 16 loop, including the
+                                final one that only tests for termination      */
+    int64_t brick_marches;   /* local marches of a brick (both phases)           */
+    int64_t march_rounds;    /* bucket rounds summed over all brick marches      */
+    int64_t exchanges;       /* brick faces that sent changed overlap data       */
+    int64_t accepted;        /* cell acceptances (re-acceptances counted again)  */
+    int64_t n_bricks;        /* bricks of the grid                               */
+    int32_t error_flags;     /* device-side error bits (0 = none)                */
+    int32_t reserved0;
+} fmm_stats;
+
+typedef struct fmm_handle fmm_handle;
+
+/*
+ * fmm_create -- allocate a solver for one grid and load its speed field.
+ *   cfg          : host pointer, copied.
+ *   speed        : device, nx*ny*nz values of F (dtype), all finite and > 0;
+ *                  or NULL for the constant speed_const (> 0).
+ *   src_ijk      : host, n_src (i, j, k) int64 triples: the point sources used
+ *                  by fmm_solve (psi = 0, KNOWN_FIX; Algorithm 8); may be NULL
+ *                  when n_src == 0.
+ *   out          : receives the handle (owned by the caller; fmm_destroy).
+ * The handle owns all device workspace (brick-layout psi and tags, per-brick
+ * front minima and exchange masks, work lists, the restart control block and,
+ * when record_tape is set, the upwind tape).
+ */
+fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_const,
+                      const int64_t *src_ijk, int64_t n_src, fmm_handle **out);
+
+/*
+ * fmm_set_speed -- replace the speed field of an existing handle (same rules
+ * as fmm_create's speed/speed_const); invalidates any recorded tape.
+ */
+fmm_status fmm_set_speed(fmm_handle *hd, const void *speed, double speed_const);
+
+/*
+ * fmm_solve -- point-source solve (Algorithm 16 with the sources of
+ * fmm_create).  T_out: device, nx*ny*nz values of psi (dtype); tags_out:
+ * device uint8 tags (fmm_tag) or NULL.
+ */
+fmm_status fmm_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out);
+
+/*
+ * fmm_reinit_signed_distance -- two-sided reinitialisation (Sec. 3 and
+ * Algorithm 16) of the level set phi0 (device, dtype).  Cells with a
+ * 6-neighbour of the opposite sign of phi0 (sign(0) = +1) are the interface
+ * cells (Algorithm 8): psi = sign(phi0) * (sum_a d_a^-2)^(-1/2) over the axes
+ * whose segment to a neighbour crosses the interface, d_a the smaller
+ * linear-interpolation crossing distance on axis a.  Both signs march.
+ * T_out (device, dtype) receives the signed solution; tags_out as fmm_solve.
+ */
+fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_out,
+                                      uint8_t *tags_out);
+
+/*
+ * fmm_adjoint -- reverse-mode derivative of a scalar loss L(psi) with respect
+ * to the slowness 1/F of every cell, about the last solve on this handle
+ * (which must have been run with record_tape = 1; otherwise FMM_ERR_STATE).
+ * The discrete Eq. (2) at an accepted non-FIX cell p with final upwind set
+ * U(p) reads sum_{i in U(p)} ((psi_p - psi_i)/h)^2 = s_p^2, which gives
+ * dpsi_p/ds_p = s_p/D_p and dpsi_p/dpsi_i = (psi_p - psi_i)/(h^2 D_p) with
+ * D_p = sum_i (psi_p - psi_i)/h^2; these are applied in decreasing psi.
+ * FIX cells get zero.  dL_dT: device (dtype), dL/dpsi; dL_dslowness: device
+ * (dtype), written.  (This derivative is not part of the paper.)
+ */
+fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness);
+
+/* fmm_get_stats -- statistics of the last solve (synchronises the stream). */
+fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out);
+
+/* fmm_last_error -- message of the last failing call on hd, or of the last
+ * failing fmm_create on this thread when hd is NULL.  Never NULL. */
+const char *fmm_last_error(const fmm_handle *hd);
+
+/* fmm_destroy -- free the handle and its workspace (NULL is allowed). */
+void fmm_destroy(fmm_handle *hd);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

@@ -1,0 +1,352 @@
+// fmm_api.cu -- the C ABI of libfmm_gb300.so (declared in include/fmm.h):
+// handle lifecycle, argument checking, device workspace and the host side of
+// the restart loop of Algorithm 16.
+#include "fmm.h"
+#include "fmm_internal.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fmmgb;
+
+struct fmm_handle {
+    fmm_config cfg;
+    Geom geom;
+    SolveParams params;
+    DeviceState st;
+    cudaStream_t stream = nullptr;
+    size_t rsize = 4;
+    double speed_const = 1.0;
+    long long *d_src = nullptr;
+    long long n_src = 0;
+    Control *h_ctrl = nullptr;   // pinned host mirror of the control block
+    bool solved = false;
+    bool tape_valid = false;
+    fmm_stats stats;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+fmm_status fail(fmm_handle *hd, fmm_status code, const std::string &msg)
+{
+    if (hd)
+        hd->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+fmm_status cuda_fail(fmm_handle *hd, cudaError_t e, const char *where)
+{
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(hd, e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, msg);
+}
+
+#define FMM_CUDA(hd, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess)                              \
+            return cuda_fail((hd), e_, #call);              \
+    } while (0)
+
+void free_state(fmm_handle *hd)
+{
+    DeviceState &s = hd->st;
+    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.dirty,
+                    s.list[0], s.list[1], s.ctrl, hd->d_src};
+    for (void *p : ptrs)
+        if (p)
+            cudaFree(p);
+    if (hd->h_ctrl)
+        cudaFreeHost(hd->h_ctrl);
+    memset(&hd->st, 0, sizeof(hd->st));
+    hd->d_src = nullptr;
+    hd->h_ctrl = nullptr;
+}
+
+template <typename T>
+cudaError_t alloc(T **p, size_t bytes)
+{
+    return cudaMalloc((void **)p, bytes < 16 ? 16 : bytes);
+}
+
+fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
+{
+    if (!speed && !(speed_const > 0.0 && std::isfinite(speed_const)))
+        return fail(hd, FMM_ERR_INVALID, "speed_const must be finite and > 0 when speed is NULL");
+    DeviceState &s = hd->st;
+    const size_t cells = (size_t)hd->geom.nbricks * kB3;
+    if (speed && !s.spd)
+        FMM_CUDA(hd, alloc(&s.spd, cells * hd->rsize));
+    if (!speed && s.spd) {
+        cudaFree(s.spd);
+        s.spd = nullptr;
+    }
+    hd->speed_const = speed ? 1.0 : speed_const;
+    FMM_CUDA(hd, launch_reset_control(s, hd->stream));
+    FMM_CUDA(hd, launch_load_speed(hd->cfg.dtype, hd->geom, s, hd->params.h, speed,
+                                   hd->speed_const, hd->stream));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost,
+                                 hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    if (hd->h_ctrl->error & ERR_SPEED)
+        return fail(hd, FMM_ERR_INVALID, "speed values must be finite and > 0");
+    // the constant-speed term of the quadratic: 1/F^2 (fp64) or (h/F)^2 (fp32)
+    hd->params.spd_term = 0.0;
+    if (!speed) {
+        if (hd->cfg.dtype == FMM_F64) {
+            hd->params.spd_term = 1.0 / (speed_const * speed_const);
+        } else {
+            const float hf = (float)hd->params.h;
+            const float F = (float)speed_const;
+            hd->params.spd_term = (double)((hf * hf) / (F * F));
+        }
+    }
+    hd->tape_valid = false;
+    return FMM_OK;
+}
+
+// Algorithm 9, then the loop of Algorithm 16, then the output conversion.
+fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
+{
+    DeviceState &s = hd->st;
+    const Geom &g = hd->geom;
+    const int dt = hd->cfg.dtype;
+    cudaStream_t st = hd->stream;
+    FMM_CUDA(hd, launch_reset_control(s, st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
+    // The loop of Algorithm 16 runs on the device; the host enqueues restarts
+    // in growing batches and reads the termination flag between batches
+    // (restarts enqueued after termination return at once).
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit_s = hd->cfg.timeout_s > 0 ? (double)hd->cfg.timeout_s : 600.0;
+    bool timed_out = false;
+    long long batch = 1;
+    for (;;) {
+        for (long long r = 0; r < batch; ++r)
+            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st));
+        FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA(hd, cudaStreamSynchronize(st));
+        if (hd->h_ctrl->done)
+            break;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit_s) {
+            timed_out = true;
+            break;
+        }
+        if (batch < 16)
+            batch *= 2;
+    }
+    const Control &c = *hd->h_ctrl;
+    hd->stats.restarts = c.restart;
+    hd->stats.brick_marches = (int64_t)c.marches;
+    hd->stats.march_rounds = (int64_t)c.rounds;
+    hd->stats.exchanges = (int64_t)c.exchanges;
+    hd->stats.accepted = (int64_t)c.accepted;
+    hd->stats.n_bricks = g.nbricks;
+    hd->stats.error_flags = c.error;
+    if (T_out)
+        FMM_CUDA(hd, launch_output(dt, g, s, T_out, tags_out, st));
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    hd->solved = true;
+    hd->tape_valid = s.tape != nullptr;
+    if (timed_out)
+        return fail(hd, FMM_ERR_TIMEOUT, "the solve exceeded its wall-clock limit (timeout_s)");
+    if (c.error & ERR_ROUNDS)
+        return fail(hd, FMM_ERR_TIMEOUT, "a brick march exceeded its round limit");
+    if (c.error & ERR_RESTARTS)
+        return fail(hd, FMM_ERR_TIMEOUT, "the restart limit was reached before termination");
+    return FMM_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_const,
+                      const int64_t *src_ijk, int64_t n_src, fmm_handle **out)
+{
+    if (!out)
+        return fail(nullptr, FMM_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    if (!cfg)
+        return fail(nullptr, FMM_ERR_INVALID, "cfg must not be NULL");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->nx > (1 << 20) || cfg->ny > (1 << 20) ||
+        cfg->nz > (1 << 20))
+        return fail(nullptr, FMM_ERR_INVALID, "grid sizes must be in [1, 2^20]");
+    if (!(cfg->h > 0.0) || !std::isfinite(cfg->h))
+        return fail(nullptr, FMM_ERR_INVALID, "h must be finite and > 0");
+    if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
+        return fail(nullptr, FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
+    if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
+        cfg->bucket < 0.0 || std::isnan(cfg->bucket))
+        return fail(nullptr, FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
+    if (n_src < 0 || (n_src > 0 && !src_ijk))
+        return fail(nullptr, FMM_ERR_INVALID, "bad source list");
+    if (speed && !aligned16(speed))
+        return fail(nullptr, FMM_ERR_INVALID, "speed must be 16-byte aligned");
+    for (int64_t i = 0; i < n_src; ++i) {
+        const int64_t a = src_ijk[3 * i], b = src_ijk[3 * i + 1], c = src_ijk[3 * i + 2];
+        if (a < 0 || a >= cfg->nx || b < 0 || b >= cfg->ny || c < 0 || c >= cfg->nz)
+            return fail(nullptr, FMM_ERR_INVALID, "source cell outside the grid");
+    }
+    fmm_handle *hd = new (std::nothrow) fmm_handle();
+    if (!hd)
+        return fail(nullptr, FMM_ERR_OOM, "host allocation failed");
+    hd->cfg = *cfg;
+    hd->stream = (cudaStream_t)cfg->stream;
+    hd->rsize = cfg->dtype == FMM_F64 ? 8 : 4;
+    memset(&hd->stats, 0, sizeof(hd->stats));
+    memset(&hd->st, 0, sizeof(hd->st));
+    Geom &g = hd->geom;
+    g.nx = (int)cfg->nx;
+    g.ny = (int)cfg->ny;
+    g.nz = (int)cfg->nz;
+    g.nbx = (g.nx + kB - 1) / kB;
+    g.nby = (g.ny + kB - 1) / kB;
+    g.nbz = (g.nz + kB - 1) / kB;
+    g.nbricks = (long long)g.nbx * g.nby * g.nbz;
+    SolveParams &p = hd->params;
+    p.h = cfg->h;
+    const double hh = 1.0 / cfg->h;
+    p.w = hh * hh;
+    p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
+    const double stride_h = cfg->stride > 0.0 ? cfg->stride : 2.0;
+    p.stride = stride_h * cfg->h;
+    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : 1.0;
+    p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
+    p.max_rounds = 1 << 22;
+
+    auto bail = [&](fmm_status code) {
+        g_create_error = hd->err;
+        free_state(hd);
+        delete hd;
+        return code;
+    };
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return bail(cuda_fail(hd, e, "cudaGetDevice"));
+    DeviceState &s = hd->st;
+    const size_t nb = (size_t)g.nbricks, cells = nb * kB3;
+#define ALLOC(ptr, bytes)                                          \
+    do {                                                           \
+        cudaError_t e2 = alloc(&(ptr), (bytes));                   \
+        if (e2 != cudaSuccess)                                     \
+            return bail(cuda_fail(hd, e2, "cudaMalloc " #ptr));     \
+    } while (0)
+    ALLOC(s.T, cells * hd->rsize);
+    ALLOC(s.tag, cells);
+    ALLOC(s.bdelta, nb * hd->rsize);
+    ALLOC(s.bmin, 2 * nb * hd->rsize);
+    ALLOC(s.fresh, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.dirty, nb * sizeof(unsigned));
+    ALLOC(s.list[0], nb * sizeof(int));
+    ALLOC(s.list[1], nb * sizeof(int));
+    ALLOC(s.ctrl, sizeof(Control));
+    if (cfg->record_tape)
+        ALLOC(s.tape, cells);
+    if (n_src > 0) {
+        ALLOC(hd->d_src, (size_t)n_src * 3 * sizeof(long long));
+        e = cudaMemcpy(hd->d_src, src_ijk, (size_t)n_src * 3 * sizeof(long long), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return bail(cuda_fail(hd, e, "cudaMemcpy sources"));
+    }
+#undef ALLOC
+    hd->n_src = n_src;
+    e = cudaMallocHost((void **)&hd->h_ctrl, sizeof(Control));
+    if (e != cudaSuccess)
+        return bail(cuda_fail(hd, e, "cudaMallocHost"));
+    const int per_sm = march_blocks_per_sm(cfg->dtype);
+    s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
+    fmm_status rc = load_speed(hd, speed, speed_const);
+    if (rc != FMM_OK)
+        return bail(rc);
+    *out = hd;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_speed(fmm_handle *hd, const void *speed, double speed_const)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (speed && !aligned16(speed))
+        return fail(hd, FMM_ERR_INVALID, "speed must be 16-byte aligned");
+    return load_speed(hd, speed, speed_const);
+}
+
+fmm_status fmm_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!T_out || !aligned16(T_out))
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+    FMM_CUDA(hd, launch_init_sources(hd->cfg.dtype, hd->geom, hd->st, hd->d_src, hd->n_src, hd->stream));
+    return run_solve(hd, T_out, tags_out);
+}
+
+fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_out,
+                                      uint8_t *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!phi0 || !aligned16(phi0))
+        return fail(hd, FMM_ERR_INVALID, "phi0 must be a 16-byte aligned device pointer");
+    if (!T_out || !aligned16(T_out))
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+    FMM_CUDA(hd, launch_init_reinit(hd->cfg.dtype, hd->geom, hd->st, hd->params, phi0, hd->stream));
+    return run_solve(hd, T_out, tags_out);
+}
+
+fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!dL_dT || !dL_dslowness)
+        return fail(hd, FMM_ERR_INVALID, "dL_dT and dL_dslowness must be device pointers");
+    if (!hd->solved || !hd->tape_valid)
+        return fail(hd, FMM_ERR_STATE, "fmm_adjoint needs a solve with record_tape = 1 first");
+    return fail(hd, FMM_ERR_STATE, "adjoint kernel not available in this build");
+}
+
+fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out)
+{
+    if (!hd || !out)
+        return FMM_ERR_INVALID;
+    *out = hd->stats;
+    return FMM_OK;
+}
+
+const char *fmm_last_error(const fmm_handle *hd)
+{
+    if (!hd)
+        return g_create_error.c_str();
+    return hd->err.c_str();
+}
+
+void fmm_destroy(fmm_handle *hd)
+{
+    if (!hd)
+        return;
+    if (hd->stream)
+        cudaStreamSynchronize(hd->stream);
+    else
+        cudaDeviceSynchronize();
+    free_state(hd);
+    delete hd;
+}
+
+}  // extern "C"

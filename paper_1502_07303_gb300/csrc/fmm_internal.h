@@ -1,0 +1,113 @@
+// fmm_internal.h -- declarations shared by the translation units of
+// libfmm_gb300.so.  Not part of the public ABI (that is include/fmm.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fmmgb {
+
+// ---------------------------------------------------------------------------
+// Brick decomposition.  The grid is cut into 8x8x8 bricks; each brick plays
+// the role of one subdomain Omega_p of Sec. 4.1 and its one-cell face halo the
+// ghost layer Theta_p.  Brick-major layout: brick id = (bz*nby + by)*nbx + bx,
+// the 512 cells of a brick contiguous, x fastest inside the brick.
+// ---------------------------------------------------------------------------
+constexpr int kB = 8;
+constexpr int kB3 = 512;
+constexpr int kTile = 10;          // brick plus one halo layer per side
+constexpr int kTile3 = 1000;
+constexpr int kFaces = 6;          // -x, +x, -y, +y, -z, +z
+constexpr int kThreads = 512;      // one thread per brick cell
+
+// Cell tag (brick layout).  Bits 0-1: status; bit 2: side -1; bit 3: padding
+// cell beyond the grid.  The status values equal the public fmm_tag values.
+enum : uint8_t {
+    ST_FAR = 0,
+    ST_BAND = 1,
+    ST_KNOWN = 2,
+    ST_FIX = 3,
+    ST_MASK = 3,
+    TG_NEG = 4,
+    TG_OUT = 8,
+};
+
+// Device-side error bits (Control::error).
+enum : int {
+    ERR_ROUNDS = 1,       // a brick march exceeded its round limit
+    ERR_RESTARTS = 2,     // the restart limit was reached
+    ERR_SPEED = 4,        // a speed value was not finite and > 0
+};
+
+// Restart control block of Algorithm 16, in device memory.
+struct Control {
+    unsigned long long minbits[2];   // min |psi| over BAND cells per side
+                                     // (bits of a non-negative double)
+    unsigned long long marches;      // statistics
+    unsigned long long rounds;
+    unsigned long long exchanges;
+    unsigned long long accepted;
+    double bound[2];                 // bound_band(-1), bound_band(+1)
+    unsigned int dirty_count;        // count_global: bricks with pending
+                                     // overlap changes
+    unsigned int n_list[2];          // lengths of the two work lists
+    int done;
+    int error;
+    int restart;
+    int pad;
+};
+
+struct Geom {
+    int nx, ny, nz;
+    int nbx, nby, nbz;
+    long long nbricks;
+};
+
+// Parameters of one solve.
+struct SolveParams {
+    double h;
+    double w;           // (1/h)^2, the h_i^2 of Algorithm 11
+    double width;       // width_band
+    double stride;      // delta_s (absolute units)
+    double bucket;      // bucket width factor
+    double spd_term;    // speed term of a constant speed: 1/F^2 (fp64), (h/F)^2 (fp32)
+    long long max_restarts;
+    int max_rounds;     // per brick march
+};
+
+// Device buffers owned by a handle (typed by the launchers).
+struct DeviceState {
+    void *T;            // |psi| per cell, brick layout
+    uint8_t *tag;       // tag per cell, brick layout
+    void *spd;          // speed term per cell (brick layout) or null
+    void *bdelta;       // per-brick bucket width (h * min slowness / sqrt 3)
+    uint8_t *tape;      // upwind set per cell or null
+    void *bmin;         // 2 per brick: min |psi| of BAND cells per side
+    unsigned long long *fresh;   // 6 per brick: changed-halo masks
+    unsigned int *dirty;         // 1 per brick: has pending overlap changes
+    int *list[2];       // work lists
+    Control *ctrl;
+    int march_ctas;
+};
+
+// Launchers (fmm_march.cu).  All enqueue on `stream`; `dtype` is 0 for float
+// and 1 for double.
+cudaError_t launch_init_sources(int dtype, const Geom &g, const DeviceState &s,
+                                const long long *src_ijk, long long n_src,
+                                cudaStream_t stream);
+cudaError_t launch_init_reinit(int dtype, const Geom &g, const DeviceState &s,
+                               const SolveParams &p, const void *phi0,
+                               cudaStream_t stream);
+cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s,
+                              double h, const void *speed, double speed_const,
+                              cudaStream_t stream);
+cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
+                              const SolveParams &p, cudaStream_t stream);
+cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
+                           const SolveParams &p, cudaStream_t stream);
+cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
+cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
+                          void *T_out, uint8_t *tags_out, cudaStream_t stream);
+int march_blocks_per_sm(int dtype);
+
+}  // namespace fmmgb

@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libfmm_gb300.so (C ABI in include/fmm.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies device memory and the current stream.  Importing this module
+loads the library and fails loudly if it is missing or was not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FMM_OK, FMM_ERR_INVALID, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE = range(6)
+FMM_F32, FMM_F64 = 0, 1
+TAG_FAR, TAG_BAND, TAG_KNOWN, TAG_FIX = 0, 1, 2, 3
+
+EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
+            "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy")
+
+
+class FmmConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("h", ctypes.c_double), ("dtype", ctypes.c_int32),
+                ("record_tape", ctypes.c_int32), ("width", ctypes.c_double),
+                ("stride", ctypes.c_double), ("bucket", ctypes.c_double),
+                ("ctas", ctypes.c_int32), ("timeout_s", ctypes.c_int32),
+                ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class FmmStats(ctypes.Structure):
+    _fields_ = [("restarts", ctypes.c_int64), ("brick_marches", ctypes.c_int64),
+                ("march_rounds", ctypes.c_int64), ("exchanges", ctypes.c_int64),
+                ("accepted", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
+                ("error_flags", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fmm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) and bind the shared library."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.build()
+    if not os.path.exists(p):
+        raise FmmError(FMM_ERR_STATE, f"CUDA library not found at {p}")
+    lib = ctypes.CDLL(p)
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.fmm_create.argtypes = [ctypes.POINTER(FmmConfig), vp, dbl, vp, i64, ctypes.POINTER(vp)]
+    lib.fmm_set_speed.argtypes = [vp, vp, dbl]
+    lib.fmm_solve.argtypes = [vp, vp, vp]
+    lib.fmm_reinit_signed_distance.argtypes = [vp, vp, vp, vp]
+    lib.fmm_adjoint.argtypes = [vp, vp, vp]
+    lib.fmm_get_stats.argtypes = [vp, ctypes.POINTER(FmmStats)]
+    lib.fmm_last_error.argtypes = [vp]
+    lib.fmm_last_error.restype = ctypes.c_char_p
+    lib.fmm_destroy.argtypes = [vp]
+    lib.fmm_destroy.restype = None
+    for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
+              "fmm_adjoint", "fmm_get_stats"):
+        getattr(lib, n).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dtype_code(dtype):
+    if dtype in (torch.float32, "f32", "float32", np.float32):
+        return FMM_F32, torch.float32
+    if dtype in (torch.float64, "f64", "float64", np.float64):
+        return FMM_F64, torch.float64
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _dev_ptr(t: torch.Tensor, dtype=None, shape=None, name="array"):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One handle of the CUDA library: a grid (nz, ny, nx), spacing h, dtype,
+    a speed field (tensor on the device or a constant) and optional point
+    sources (i, j, k)."""
+
+    def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
+                 width=math.inf, stride=2.0, bucket=1.0, record_tape=False, ctas=0,
+                 max_restarts=0, timeout_s=0, stream=None):
+        self.lib = load()
+        nz, ny, nx = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.code, self.dtype = _dtype_code(dtype)
+        self.stream = stream
+        cfg = FmmConfig()
+        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        cfg.h = float(h)
+        cfg.dtype = self.code
+        cfg.record_tape = 1 if record_tape else 0
+        cfg.width = 0.0 if math.isinf(width) else float(width)
+        cfg.stride = float(stride)
+        cfg.bucket = float(bucket)
+        cfg.ctas = int(ctas)
+        cfg.max_restarts = int(max_restarts)
+        cfg.timeout_s = int(timeout_s)
+        cfg.stream = _stream_handle(stream)
+        self.cfg = cfg
+        sp_ptr, sp_const = self._speed_args(speed)
+        src = None
+        n_src = 0
+        if sources is not None:
+            src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1, 3))
+            n_src = len(src)
+        handle = ctypes.c_void_p()
+        rc = self.lib.fmm_create(ctypes.byref(cfg), sp_ptr, sp_const,
+                                 None if src is None else src.ctypes.data, n_src,
+                                 ctypes.byref(handle))
+        if rc != FMM_OK:
+            raise FmmError(rc, self.lib.fmm_last_error(None).decode())
+        self.handle = handle
+        self.h = float(h)
+
+    def _speed_args(self, speed):
+        if speed is None:
+            return None, 1.0
+        if isinstance(speed, (int, float)):
+            return None, float(speed)
+        self._speed_ref = speed
+        return _dev_ptr(speed, self.dtype, self.shape, "speed"), 0.0
+
+    def _check(self, rc):
+        if rc != FMM_OK:
+            raise FmmError(rc, self.lib.fmm_last_error(self.handle).decode())
+
+    def set_speed(self, speed):
+        p, c = self._speed_args(speed)
+        self._check(self.lib.fmm_set_speed(self.handle, p, c))
+
+    def _outputs(self, T_out, tags_out, want_tags):
+        if T_out is None:
+            T_out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        if tags_out is None and want_tags:
+            tags_out = torch.empty(self.shape, dtype=torch.uint8, device="cuda")
+        tp = _dev_ptr(T_out, self.dtype, self.shape, "T_out")
+        gp = None if tags_out is None else _dev_ptr(tags_out, torch.uint8, self.shape, "tags_out")
+        return T_out, tags_out, tp, gp
+
+    def solve(self, T_out=None, tags_out=None, want_tags=True):
+        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
+        self._check(self.lib.fmm_solve(self.handle, tp, gp))
+        return T_out, tags_out
+
+    def reinit(self, phi0, T_out=None, tags_out=None, want_tags=True):
+        pp = _dev_ptr(phi0, self.dtype, self.shape, "phi0")
+        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
+        self._check(self.lib.fmm_reinit_signed_distance(self.handle, pp, tp, gp))
+        return T_out, tags_out
+
+    def adjoint(self, dL_dT, out=None):
+        gp = _dev_ptr(dL_dT, self.dtype, self.shape, "dL_dT")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        op = _dev_ptr(out, self.dtype, self.shape, "dL_dslowness")
+        self._check(self.lib.fmm_adjoint(self.handle, gp, op))
+        return out
+
+    def stats(self):
+        st = FmmStats()
+        self._check(self.lib.fmm_get_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+def solve_sources(shape, h, sources, speed=None, dtype=torch.float32, **kw):
+    """Point-source solve; returns (T, tags, stats)."""
+    with Solver(shape, h, dtype=dtype, speed=speed, sources=sources, **kw) as s:
+        T, G = s.solve()
+        return T, G, s.stats()
+
+
+def reinit(phi0, h, dtype=None, **kw):
+    """Two-sided signed-distance reinitialisation of phi0 (a CUDA tensor);
+    returns (T, tags, stats)."""
+    dtype = phi0.dtype if dtype is None else dtype
+    with Solver(tuple(phi0.shape), h, dtype=dtype, **kw) as s:
+        T, G = s.reinit(phi0.to(dtype).contiguous())
+        return T, G, s.stats()
+
+
+class EikonalFn(torch.autograd.Function):
+    """T = EikonalFn.apply(slowness, solver): point-source travel times for a
+    slowness field (1/F); backward returns dL/d(slowness) from the CUDA
+    adjoint.  ``solver`` must be a Solver created with record_tape=True."""
+
+    @staticmethod
+    def forward(ctx, slowness, solver):
+        speed = (1.0 / slowness).contiguous()
+        solver.set_speed(speed)
+        T, _ = solver.solve(want_tags=False)
+        ctx.solver = solver
+        return T
+
+    @staticmethod
+    def backward(ctx, gT):
+        g = ctx.solver.adjoint(gT.contiguous())
+        return g, None

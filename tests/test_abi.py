@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/fmm.h declares (no compute call: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(fmm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fmm_create", "fmm_solve", "fmm_reinit_signed_distance",
+                     "fmm_adjoint", "fmm_destroy", "fmm_get_stats", "fmm_last_error"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_symbol():
+    from paper_1502_07303_gb300 import build
+    path = build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_1502_07303_gb300 import fmm
+    assert set(fmm.EXPORTED) <= set(declared_functions())
+
+
+def test_create_error_without_gpu_is_reported():
+    """Argument checking happens before any CUDA call: a bad config returns
+    FMM_ERR_INVALID with a message, even on a machine without a GPU."""
+    from paper_1502_07303_gb300 import fmm
+    lib = fmm.load()
+    cfg = fmm.FmmConfig()
+    cfg.nx, cfg.ny, cfg.nz, cfg.h, cfg.dtype = 0, 4, 4, 0.1, 0
+    h = ctypes.c_void_p()
+    rc = lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h))
+    assert rc == fmm.FMM_ERR_INVALID
+    assert b"grid" in lib.fmm_last_error(None)
+    cfg.nx, cfg.h = 4, -1.0
+    assert lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h)) == fmm.FMM_ERR_INVALID
+    cfg.h, cfg.dtype = 0.1, 7
+    assert lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h)) == fmm.FMM_ERR_INVALID
+    cfg.dtype = 0
+    src = (ctypes.c_int64 * 3)(9, 0, 0)
+    assert lib.fmm_create(ctypes.byref(cfg), None, 1.0, src, 1, ctypes.byref(h)) == fmm.FMM_ERR_INVALID
+    assert b"outside" in lib.fmm_last_error(None)
+    assert lib.fmm_solve(None, None, None) == fmm.FMM_ERR_INVALID
+    lib.fmm_destroy(None)

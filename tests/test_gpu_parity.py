@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle,
+element by element on the same seeded inputs.
+
+Sizes span several 8^3 bricks and ragged tails; the oracle finishes each case
+in seconds.  Tolerances: max |dT| <= 1e-12 max|T| (fp64), 2e-5 max|T| (fp32),
+with identical tags (identical accepted sets)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1502_07303_gb300 import workloads as wl
+from parity_util import compare
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": torch.float32, "f64": torch.float64}
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is required for the gpu tests")
+    from paper_1502_07303_gb300 import fmm as _fmm
+    return _fmm
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=DT[dt])
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _quantise(a, dt):
+    """The input the GPU sees, as fp64 for the oracle."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64) if dt == "f32" else np.asarray(a, np.float64)
+
+
+def run_sources(fmm, oracle, shape, h, src, speed, dt, **kw):
+    sp_gpu = None if speed is None or np.isscalar(speed) else _dev(speed, dt)
+    sp_const = speed if np.isscalar(speed) else None
+    with fmm.Solver(shape, h, dtype=DT[dt], speed=sp_gpu if sp_gpu is not None else sp_const,
+                    sources=src, **kw) as s:
+        T, G = s.solve()
+        stats = s.stats()
+    sp_ref = None if speed is None else (speed if np.isscalar(speed) else _quantise(speed, dt))
+    width = kw.get("width", math.inf)
+    ref = oracle.solve_sources(shape, src, h, speed=sp_ref, width=width)
+    return _host(T), _host(G), ref, stats
+
+
+def run_reinit(fmm, oracle, phi, h, dt, **kw):
+    phi_q = _quantise(phi, dt)
+    with fmm.Solver(phi.shape, h, dtype=DT[dt], **kw) as s:
+        T, G = s.reinit(_dev(phi, dt))
+        stats = s.stats()
+    ref = oracle.solve_reinit(phi_q, h, width=kw.get("width", math.inf))
+    return _host(T), _host(G), ref, stats
+
+
+# ---------------------------------------------------------------------------
+# point sources, constant speed
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_point_source_64(fmm, oracle, dt):
+    p = wl.point_source(64)
+    T, G, ref, st = run_sources(fmm, oracle, p.shape, p.h, p.sources, None, dt)
+    compare(T, G, ref, dt)
+    assert st["error_flags"] == 0
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (33, 17, 9), (7, 13, 40), (1, 1, 1), (1, 5, 1),
+                                   (9, 9, 9)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_sources_shapes(fmm, oracle, shape, dt):
+    rng = np.random.default_rng(sum(shape))
+    src = wl.random_cells(rng, shape, min(3, int(np.prod(shape))))
+    h = wl.spacing(shape)
+    T, G, ref, _ = run_sources(fmm, oracle, shape, h, src, 1.7, dt)
+    compare(T, G, ref, dt)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_no_sources_all_far(fmm, oracle, dt):
+    shape = (10, 12, 9)
+    T, G, ref, st = run_sources(fmm, oracle, shape, 0.1, np.zeros((0, 3), np.int64), None, dt)
+    assert np.all(G == 0) and np.all(np.isinf(T))
+    compare(T, G, ref, dt)
+
+
+# ---------------------------------------------------------------------------
+# heterogeneous speed
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [24, 41])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_fourier_speed(fmm, oracle, n, dt):
+    p = wl.fourier_sources(n=n, n_sources=4, n_receivers=8, seed=3)
+    T, G, ref, st = run_sources(fmm, oracle, p.shape, p.h, p.sources, p.speed, dt)
+    compare(T, G, ref, dt)
+
+
+@pytest.mark.parametrize("case", [4, 5])
+def test_paper_speed_cases(fmm, oracle, case):
+    """Sec. 5.1 cases 4 and 5 (Eq. (9), (10)): point source at the centre."""
+    n = 40
+    shape = (n, n, n)
+    F = wl.paper_speed(shape, case)
+    T, G, ref, _ = run_sources(fmm, oracle, shape, 1.0 / n, [(n // 2, n // 2, n // 2)], F, "f64")
+    compare(T, G, ref, "f64")
+
+
+# ---------------------------------------------------------------------------
+# two-sided reinitialisation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (29, 41, 23)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_reinit_spheres(fmm, oracle, shape, dt):
+    p = wl.random_spheres(shape=shape, count=6, seed=7)
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, dt)
+    compare(T, G, ref, dt)
+
+
+def test_reinit_single_sphere_64(fmm, oracle):
+    p = wl.single_sphere(64)
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64")
+    compare(T, G, ref, "f64")
+
+
+# ---------------------------------------------------------------------------
+# restart parameters, narrow band, restart counts
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("stride", [0.5, 1.0, 2.0, 3.5, math.inf])
+@pytest.mark.parametrize("bucket", [1.0, math.inf])
+def test_stride_and_bucket_do_not_change_the_result(fmm, oracle, stride, bucket):
+    p = wl.random_spheres(shape=(40, 40, 40), count=5, seed=11)
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", stride=stride, bucket=bucket)
+    compare(T, G, ref, "f64")
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_narrow_band_width(fmm, oracle, dt):
+    p = wl.random_spheres(shape=(36, 36, 36), count=4, seed=5)
+    width = 0.08
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, dt, width=width)
+    compare(T, G, ref, dt, width=width)
+
+
+def test_single_brick_infinite_stride_two_restarts(fmm, oracle):
+    """Sec. 5.3: with stride = inf one subdomain finishes in two restarts (the
+    second only finds nothing left to do)."""
+    shape = (8, 8, 8)
+    T, G, ref, st = run_sources(fmm, oracle, shape, 1.0 / 8, [(1, 2, 3)], None, "f64",
+                                stride=math.inf)
+    compare(T, G, ref, "f64")
+    assert st["restarts"] == 2
+
+
+def test_restarts_scale_inversely_with_stride(fmm, oracle):
+    """Sec. 5.4: nr is about proportional to nh / delta_s."""
+    p = wl.point_source(48)
+    nr = {}
+    for stride in (1.0, 4.0):
+        with fmm.Solver(p.shape, p.h, dtype=torch.float64, sources=p.sources, stride=stride) as s:
+            s.solve()
+            nr[stride] = s.stats()["restarts"]
+    assert nr[1.0] > 2.5 * nr[4.0]
+
+
+def test_repeat_solve_same_handle(fmm, oracle):
+    p = wl.point_source(24)
+    with fmm.Solver(p.shape, p.h, dtype=torch.float64, sources=p.sources) as s:
+        T1, G1 = s.solve()
+        T2, G2 = s.solve()
+    assert torch.equal(G1, G2)
+    ref = oracle.solve_sources(p.shape, p.sources, p.h)
+    compare(_host(T2), _host(G2), ref, "f64")
+
+
+def test_invalid_speed_rejected(fmm):
+    shape = (8, 8, 8)
+    F = torch.ones(shape, dtype=torch.float64, device="cuda")
+    F[3, 3, 3] = -1.0
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.Solver(shape, 0.1, dtype=torch.float64, speed=F, sources=[(0, 0, 0)])
+    assert e.value.code == fmm.FMM_ERR_INVALID
+    F[3, 3, 3] = float("nan")
+    with pytest.raises(fmm.FmmError):
+        fmm.Solver(shape, 0.1, dtype=torch.float64, speed=F, sources=[(0, 0, 0)])
+
+
+def test_restart_limit_reports_timeout(fmm):
+    p = wl.point_source(32)
+    with fmm.Solver(p.shape, p.h, dtype=torch.float64, sources=p.sources, stride=0.5,
+                    max_restarts=3) as s:
+        with pytest.raises(fmm.FmmError) as e:
+            s.solve()
+        assert e.value.code == fmm.FMM_ERR_TIMEOUT

@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 restarted narrow band fast marching library.
+
+Workload (one "step" = one complete solve through the C ABI): two-sided
+signed-distance reinitialisation of 32 seeded random spheres with the
+sin-modulated level set on a 256^3 unit cube (16.8 M points), fp32, full
+march, stride 2h.  The metric is grid points finalised per second (Gpoints/s).
+fp64 is measured on the same workload and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own replica of
+the workload (independent problems, no collective on the data path: weak
+scaling) and the whole-job value is the points of all ranks over the slowest
+rank's time.  ``--impl reference`` times the CPU oracle (the paper's
+sequential algorithm in plain C, fp64) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s finalised (fp32/fp64) and % HBM roofline; adjoint and batched vs plain"
+UNIT = "Gpoints/s"
+N_GRID = 256
+N_SPHERES = 32
+SEED = 2
+# algorithmic bytes per finalised point of a reinitialisation: read phi0,
+# write psi and the tag once (fp32: 4 + 4 + 1, fp64: 8 + 8 + 1)
+ALG_BYTES = {"f32": 9, "f64": 17}
+REF_SAMPLE_N = 128          # oracle sample grid for the reference arm
+CPU_BASELINE_N = 192        # oracle sample grid for the cpu_baseline entry
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """Bytes per point of the march kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "k_march_traffic.txt")
+    src = os.path.join(ROOT, "paper_1502_07303_gb300", "csrc", "fmm_march.cu")
+    try:
+        rec = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != sha:
+            return None
+        return float(rec["dram_bytes_per_point"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(n):
+    """One oracle solve of the workload recipe at n^3; returns (Gpoints/s, s)."""
+    import oracle
+    from paper_1502_07303_gb300 import workloads as wl
+    oracle.build()
+    p = wl.random_spheres(n=n, count=N_SPHERES, seed=SEED)
+    t0 = time.perf_counter()
+    oracle.solve_reinit(p.phi0, p.h)
+    dt = time.perf_counter() - t0
+    return p.n_points / dt / 1e9, dt
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1502_07303_gb300 import workloads as wl
+    oracle.build()
+    p = wl.random_spheres(n=REF_SAMPLE_N, count=N_SPHERES, seed=SEED)
+    for _ in range(args.warmup):
+        oracle.solve_reinit(p.phi0, p.h)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.solve_reinit(p.phi0, p.h)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = p.n_points / (ms / 1e3) / 1e9
+    sample = (f"{N_SPHERES}-sphere reinitialisation recipe at {REF_SAMPLE_N}^3 "
+              f"({p.n_points} points) per step, oracle fp64, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"reinit random_spheres{N_SPHERES} {N_GRID}^3 (sampled at "
+                                   f"{REF_SAMPLE_N}^3)", "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream):
+    """Device-timed solves: CUDA events around each solve on the solve's
+    stream, L2 flushed (256 MiB write) before every step, outside the events."""
+    shape = p.shape
+    s = fmm.Solver(shape, p.h, dtype=dtype, time_kernels=True, stream=stream)
+    T_out = torch.empty(shape, dtype=dtype, device="cuda")
+    G_out = torch.empty(shape, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        flush.fill_(1)
+        s.reinit(phi_dev, T_out, G_out)
+    torch.cuda.synchronize()
+    step_ms, march_ms, march_l, launches = [], 0.0, 0, 0
+    stats = None
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.reinit(phi_dev, T_out, G_out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats = s.stats()
+        march_ms += stats["march_ms"]
+        march_l += stats["march_launches"]
+        launches += stats["kernel_launches"]
+    s.close()
+    return {"ms": statistics.mean(step_ms), "ms_min": min(step_ms), "march_ms": march_ms / steps,
+            "march_launches": march_l / steps, "launches": launches, "stats": stats,
+            "T": T_out}
+
+
+def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream):
+    """The user's call with host buffers: pinned phi0 -> device, solve, psi
+    back to pinned host memory, all inside the timed region of every step."""
+    shape = p.shape
+    s = fmm.Solver(shape, p.h, dtype=dtype, stream=stream)
+    phi_dev = torch.empty(shape, dtype=dtype, device="cuda")
+    T_out = torch.empty(shape, dtype=dtype, device="cuda")
+    T_host = torch.empty(shape, dtype=dtype, pin_memory=True)
+    times = []
+    for k in range(warmup + steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        phi_dev.copy_(phi_host, non_blocking=True)
+        s.reinit(phi_dev, T_out, None, want_tags=False)
+        T_host.copy_(T_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warmup:
+            times.append(e0.elapsed_time(e1))
+    s.close()
+    nbytes = phi_host.numel() * phi_host.element_size()
+    return statistics.mean(times), nbytes, T_out.numel() * T_out.element_size()
+
+
+def run_gpu(args):
+    ws, rank, local, pg = dist_setup()
+    import torch
+    from paper_1502_07303_gb300 import fmm
+    from paper_1502_07303_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    p = wl.random_spheres(n=n, count=N_SPHERES, seed=SEED, device="cuda")
+    phi64 = p.phi0.contiguous()
+    phi32 = phi64.to(torch.float32).contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pts = p.n_points
+
+    # fp32: the headline
+    barrier(pg)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t_wall = time.perf_counter()
+    r32 = measure(fmm, torch, phi32, p, torch.float32, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall_ms = 1e3 * (time.perf_counter() - t_wall)
+    clocks = sampler.stop() if sampler else None
+    ms32 = max_over_ranks(pg, r32["ms"])
+    total_pts = sum_over_ranks(pg, float(pts))
+    value = total_pts / (ms32 / 1e3) / 1e9
+
+    # fp64 on the same workload
+    r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream)
+    ms64 = max_over_ranks(pg, r64["ms"])
+
+    # end to end through the public API with host buffers (fp32)
+    phi_host = phi32.cpu().pin_memory()
+    e2e_ms, h2d, d2h = measure_e2e(fmm, torch, phi_host, p, torch.float32, args.steps,
+                                   args.warmup, stream)
+    e2e_ms = max_over_ranks(pg, e2e_ms)
+    e2e_value = total_pts / (e2e_ms / 1e3) / 1e9
+
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = peaks()
+
+    def roofline(r, dt):
+        launches = max(r["march_launches"], 1.0)
+        avg_launch_s = r["march_ms"] / launches / 1e3
+        alg_per_launch = ALG_BYTES[dt] * pts / launches
+        achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+        bpp = traffic_record() if dt == "f32" else None
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (bpp * pts / launches) if bpp else None,
+                "kernel": "k_march", "peak_kind": peak_kind,
+                "avg_launch_us": 1e3 * r["march_ms"] / launches,
+                "launches_per_step": r["march_launches"],
+                "share_of_step": r["march_ms"] / r["ms"]}
+
+    cpu_rate, cpu_s = oracle_rate(CPU_BASELINE_N) if ws == 1 else (None, None)
+    st = r32["stats"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"reinit random_spheres{N_SPHERES} {n}^3", "grid": [n, n, n],
+                   "points_per_gpu": pts, "seed": SEED, "stride_h": 2.0, "bucket": 1.0,
+                   "brick": 8, "l2": "flushed before every step (256 MiB write)",
+                   "replicas": ws, "parallelism": "independent replicas, no collective"},
+        "roofline": roofline(r32, "f32"),
+        "cpu_baseline": ({"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": f"{N_SPHERES}-sphere reinitialisation recipe at "
+                                    f"{CPU_BASELINE_N}^3, oracle fp64, 1 thread, {cpu_s:.1f} s"}
+                         if cpu_rate is not None else None),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": r32["launches"],
+        "clocks": clocks,
+        "fp64": {"value": total_pts / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
+                 "roofline": roofline(r64, "f64")},
+        "solve_stats": {k: st[k] for k in ("restarts", "brick_marches", "march_rounds",
+                                            "exchanges", "accepted", "n_bricks")},
+        "wall_ms_timed_region": wall_ms,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -69,8 +69,11 @@ typedef struct {
     int32_t ctas;          /* CTAs of the march kernel; 0 -> as many as fit     */
     int32_t timeout_s;     /* host wall-clock limit of one solve in seconds;
                               0 -> 600; exceeding it returns FMM_ERR_TIMEOUT  */
-    int64_t max_restarts;  /* 0 -> no limit other than the grid's size          */
+    int64_t max_restarts;  /* 0 -> no limit (timeout_s still applies)           */
     void *stream;          /* cudaStream_t                                      */
+    int32_t time_kernels;  /* 1: time every march launch with CUDA events on
+                              the solve's stream (fmm_stats.march_ms)         */
+    int32_t reserved1;
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */
@@ -82,6 +85,10 @@ typedef struct {
     int64_t exchanges;       /* brick faces that sent changed overlap data       */
     int64_t accepted;        /* cell acceptances (re-acceptances counted again)  */
     int64_t n_bricks;        /* bricks of the grid                               */
+    int64_t kernel_launches; /* kernels this library launched for the solve      */
+    int64_t march_launches;  /* launches of the brick-march kernel               */
+    double march_ms;         /* summed device time of those launches (only with
+                                time_kernels; else 0)                          */
     int32_t error_flags;     /* device-side error bits (0 = none)                */
     int32_t reserved0;
 } fmm_stats;

@@ -26,7 +26,9 @@ struct fmm_handle {
     Control *h_ctrl = nullptr;   // pinned host mirror of the control block
     bool solved = false;
     bool tape_valid = false;
+    long long pre_launches = 0;       // init launches of the current solve
     fmm_stats stats;
+    std::vector<cudaEvent_t> events;   // march timing pairs (time_kernels)
     std::string err;
 };
 
@@ -66,6 +68,9 @@ void free_state(fmm_handle *hd)
             cudaFree(p);
     if (hd->h_ctrl)
         cudaFreeHost(hd->h_ctrl);
+    for (cudaEvent_t e : hd->events)
+        cudaEventDestroy(e);
+    hd->events.clear();
     memset(&hd->st, 0, sizeof(hd->st));
     hd->d_src = nullptr;
     hd->h_ctrl = nullptr;
@@ -123,7 +128,11 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     FMM_CUDA(hd, launch_reset_control(s, st));
     FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    long long launches = 0;
     FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
+    launches += 2;   // control reset, front init
+    const bool timing = hd->cfg.time_kernels != 0;
+    size_t ev_used = 0;
     // The loop of Algorithm 16 runs on the device; the host enqueues restarts
     // in growing batches and reads the termination flag between batches
     // (restarts enqueued after termination return at once).
@@ -132,8 +141,20 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     bool timed_out = false;
     long long batch = 1;
     for (;;) {
-        for (long long r = 0; r < batch; ++r)
-            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st));
+        for (long long r = 0; r < batch; ++r) {
+            cudaEvent_t *ev4 = nullptr;
+            if (timing) {
+                while (hd->events.size() < ev_used + 4) {
+                    cudaEvent_t e;
+                    FMM_CUDA(hd, cudaEventCreate(&e));
+                    hd->events.push_back(e);
+                }
+                ev4 = &hd->events[ev_used];
+                ev_used += 4;
+            }
+            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st, ev4));
+            launches += kLaunchesPerRestart;
+        }
         FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
         FMM_CUDA(hd, cudaStreamSynchronize(st));
         if (hd->h_ctrl->done)
@@ -154,9 +175,26 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     hd->stats.accepted = (int64_t)c.accepted;
     hd->stats.n_bricks = g.nbricks;
     hd->stats.error_flags = c.error;
-    if (T_out)
+    if (T_out) {
         FMM_CUDA(hd, launch_output(dt, g, s, T_out, tags_out, st));
+        launches += 1;
+    }
     FMM_CUDA(hd, cudaStreamSynchronize(st));
+    // restarts after the terminating pass only return; the march launches
+    // that did work are the two of every pass but the last
+    const long long worked = c.restart > 0 ? 2LL * (c.restart - 1) : 0;
+    hd->stats.march_launches = worked;
+    hd->stats.kernel_launches = launches + hd->pre_launches;
+    hd->pre_launches = 0;
+    double ms = 0.0;
+    if (timing) {
+        for (long long k = 0; k < worked && (size_t)(2 * k + 1) < ev_used; ++k) {
+            float e = 0.f;
+            FMM_CUDA(hd, cudaEventElapsedTime(&e, hd->events[2 * k], hd->events[2 * k + 1]));
+            ms += e;
+        }
+    }
+    hd->stats.march_ms = ms;
     hd->solved = true;
     hd->tape_valid = s.tape != nullptr;
     if (timed_out)
@@ -295,6 +333,7 @@ fmm_status fmm_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     if (!T_out || !aligned16(T_out))
         return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
     FMM_CUDA(hd, launch_init_sources(hd->cfg.dtype, hd->geom, hd->st, hd->d_src, hd->n_src, hd->stream));
+    hd->pre_launches = hd->n_src > 0 ? 2 : 1;
     return run_solve(hd, T_out, tags_out);
 }
 
@@ -308,6 +347,7 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
     if (!T_out || !aligned16(T_out))
         return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
     FMM_CUDA(hd, launch_init_reinit(hd->cfg.dtype, hd->geom, hd->st, hd->params, phi0, hd->stream));
+    hd->pre_launches = 1;
     return run_solve(hd, T_out, tags_out);
 }
 

@@ -103,8 +103,12 @@ cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s,
                               cudaStream_t stream);
 cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
                               const SolveParams &p, cudaStream_t stream);
+// One pass of the Algorithm 16 loop: reduce, control, and the two
+// select + march phases (6 launches).  ev4, when not null, holds two event
+// pairs recorded around the two march launches.
+constexpr int kLaunchesPerRestart = 6;
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
-                           const SolveParams &p, cudaStream_t stream);
+                           const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev4);
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);

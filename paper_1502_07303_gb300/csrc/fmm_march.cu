@@ -762,7 +762,7 @@ int grid_for(long long n, int threads, int cap)
 
 template <typename real>
 cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
-                         cudaStream_t st)
+                         cudaStream_t st, cudaEvent_t *ev4)
 {
     const int rb = grid_for(g.nbricks, 256, 4096);
     const bool het = s.spd != nullptr;
@@ -772,10 +772,14 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     for (int which = 0; which < 2; ++which) {
         k_select<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl,
                                            s.list[which], which);
+        if (ev4)
+            cudaEventRecord(ev4[2 * which], st);
         if (het)
             k_march<real, true, 1><<<s.march_ctas, kThreads, 0, st>>>(g, s, p, sct, which);
         else
             k_march<real, false, 1><<<s.march_ctas, kThreads, 0, st>>>(g, s, p, sct, which);
+        if (ev4)
+            cudaEventRecord(ev4[2 * which + 1], st);
     }
     return cudaGetLastError();
 }
@@ -848,9 +852,9 @@ cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
 }
 
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
-                           cudaStream_t st)
+                           cudaStream_t st, cudaEvent_t *ev4)
 {
-    return dtype == 1 ? restart_impl<double>(g, s, p, st) : restart_impl<float>(g, s, p, st);
+    return dtype == 1 ? restart_impl<double>(g, s, p, st, ev4) : restart_impl<float>(g, s, p, st, ev4);
 }
 
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st)

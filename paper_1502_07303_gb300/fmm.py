@@ -29,17 +29,21 @@ class FmmConfig(ctypes.Structure):
                 ("record_tape", ctypes.c_int32), ("width", ctypes.c_double),
                 ("stride", ctypes.c_double), ("bucket", ctypes.c_double),
                 ("ctas", ctypes.c_int32), ("timeout_s", ctypes.c_int32),
-                ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("time_kernels", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int64), ("brick_marches", ctypes.c_int64),
                 ("march_rounds", ctypes.c_int64), ("exchanges", ctypes.c_int64),
                 ("accepted", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("march_launches", ctypes.c_int64),
+                ("march_ms", ctypes.c_double),
                 ("error_flags", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if not k.startswith("reserved")}
+        return {k: (float(getattr(self, k)) if k == "march_ms" else int(getattr(self, k)))
+                for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
 class FmmError(RuntimeError):
@@ -115,7 +119,7 @@ class Solver:
 
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=2.0, bucket=1.0, record_tape=False, ctas=0,
-                 max_restarts=0, timeout_s=0, stream=None):
+                 max_restarts=0, timeout_s=0, time_kernels=False, stream=None):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
@@ -132,6 +136,7 @@ class Solver:
         cfg.ctas = int(ctas)
         cfg.max_restarts = int(max_restarts)
         cfg.timeout_s = int(timeout_s)
+        cfg.time_kernels = 1 if time_kernels else 0
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)

@@ -159,6 +159,32 @@ const char *fmm_last_error(const fmm_handle *hd);
 /* fmm_destroy -- free the handle and its workspace (NULL is allowed). */
 void fmm_destroy(fmm_handle *hd);
 
+/*
+ * fmm_reinit_signed_distance_noalloc -- the same two-sided reinitialisation
+ * as fmm_reinit_signed_distance with speed F = 1, for callers that cannot
+ * allocate device memory when they solve: code running while a stream is
+ * captured into a CUDA graph (where cudaMalloc is not allowed), processes
+ * whose device memory belongs to a pool that forbids further allocations,
+ * and loops that cannot afford an allocation.  The paper has no counterpart;
+ * this is a packaging of the solve, not a different method.
+ *   cfg      : host; nx, ny, nz, h, dtype, width, stride, bucket, ctas,
+ *              max_restarts, timeout_s and stream are used; record_tape must
+ *              be 0 (no adjoint); no handle is created.
+ *   phi0     : device (dtype), the level set; T_out: device (dtype), psi;
+ *   tags_out : device uint8 tags or NULL.
+ * No memory is allocated: the workspace is one file-scope device array of
+ * about 2.4 MiB that every GPU loading the library holds until the process
+ * exits.  Limit: at most 512 bricks of 8x8x8 cells (for example a 64^3 grid);
+ * larger grids return FMM_ERR_INVALID.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array and each call clears what it needs; calls whose GPU work overlaps on
+ * the same device (e.g. on two streams) race and give undefined results.
+ * Errors are reported through fmm_last_error(NULL).
+ */
+fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, const void *phi0, void *T_out,
+                                              uint8_t *tags_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -210,6 +210,12 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
+namespace fmmgb {
+// The message fmm_last_error(NULL) returns on this thread (used by entry
+// points that have no handle).
+void set_create_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace fmmgb
+
 extern "C" {
 
 fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_const,

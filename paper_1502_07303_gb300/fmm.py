@@ -20,7 +20,8 @@ FMM_F32, FMM_F64 = 0, 1
 TAG_FAR, TAG_BAND, TAG_KNOWN, TAG_FIX = 0, 1, 2, 3
 
 EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
-            "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy")
+            "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
+            "fmm_reinit_signed_distance_noalloc")
 
 
 class FmmConfig(ctypes.Structure):
@@ -79,8 +80,9 @@ def load(path: str | None = None):
     lib.fmm_last_error.restype = ctypes.c_char_p
     lib.fmm_destroy.argtypes = [vp]
     lib.fmm_destroy.restype = None
+    lib.fmm_reinit_signed_distance_noalloc.argtypes = [ctypes.POINTER(FmmConfig), vp, vp, vp]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
-              "fmm_adjoint", "fmm_get_stats"):
+              "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -236,6 +238,32 @@ def reinit(phi0, h, dtype=None, **kw):
     with Solver(tuple(phi0.shape), h, dtype=dtype, **kw) as s:
         T, G = s.reinit(phi0.to(dtype).contiguous())
         return T, G, s.stats()
+
+
+def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=2.0, bucket=1.0,
+                   stream=None):
+    """Reinitialisation (F = 1) through fmm_reinit_signed_distance_noalloc,
+    for callers that cannot allocate device memory: the library allocates
+    nothing, and the caller supplies phi0, T_out and (optionally) tags_out as
+    CUDA tensors.  Grids of at most 512 8x8x8 bricks (e.g. 64^3)."""
+    lib = load()
+    code, dt = _dtype_code(phi0.dtype)
+    nz, ny, nx = phi0.shape
+    cfg = FmmConfig()
+    cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+    cfg.h = float(h)
+    cfg.dtype = code
+    cfg.width = 0.0 if math.isinf(width) else float(width)
+    cfg.stride = float(stride)
+    cfg.bucket = float(bucket)
+    cfg.stream = _stream_handle(stream)
+    pp = _dev_ptr(phi0, dt, (nz, ny, nx), "phi0")
+    tp = _dev_ptr(T_out, dt, (nz, ny, nx), "T_out")
+    gp = None if tags_out is None else _dev_ptr(tags_out, torch.uint8, (nz, ny, nx), "tags_out")
+    rc = lib.fmm_reinit_signed_distance_noalloc(ctypes.byref(cfg), pp, tp, gp)
+    if rc != FMM_OK:
+        raise FmmError(rc, lib.fmm_last_error(None).decode())
+    return T_out, tags_out
 
 
 class EikonalFn(torch.autograd.Function):

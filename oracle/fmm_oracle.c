@@ -267,30 +267,46 @@ static int32_t remove_min(march_t *m, heap_t *hp)
 
 /* psi[a], hh[a] per axis as in Algorithm 11 (hh = 1/h or 0); dir[a] is the
  * chosen neighbour direction (-1, +1 or 0).  Returns psi_temp and the upwind
- * set of the root that produced it (2 bits per axis, see the header). */
+ * set of the root that produced it (2 bits per axis, see the header).
+ *
+ * The quadratic of Algorithm 11, sum_i h_i^2 (t - psi_i)^2 = F^-2, is solved
+ * for the unknown shifted by the smallest upwind value m: t = m + u with
+ * delta_i = psi_i - m, giving a = sum h_i^2, b = -2 sum h_i^2 delta_i and
+ * c = sum h_i^2 delta_i^2 - F^-2.  It is the same equation; written in psi
+ * itself, b^2 and 4ac are of order (psi/h)^2 while b^2 - 4ac is of order
+ * (1/(hF))^2, so rounding would cost about 3 (psi F/h)^2 ulp in the
+ * discriminant (1e-10 relative at 1024^3), far from the machine-accuracy
+ * agreement of parallel and sequential solutions reported in Sec. 5.2.  The
+ * causality test psi_i < t reads delta_i < u in the shifted unknown. */
 static double quadratic_roots(double psi[3], double hh[3], const int dir[3],
                               double Finv2, uint8_t *set_out)
 {
     uint8_t cur = 0;
     int nd = 0;
+    double m = OR_INF;
     for (int a = 0; a < 3; ++a) {
         if (hh[a] != 0.0) {
             nd += 1;
             cur |= (uint8_t)((dir[a] < 0 ? 1 : 2) << (2 * a));
+            if (psi[a] < m)
+                m = psi[a];
         }
     }
     double psi_temp = OR_INF;
     uint8_t best_set = 0;
     while (nd != 0) {
+        double d0 = hh[0] != 0.0 ? psi[0] - m : 0.0;
+        double d1 = hh[1] != 0.0 ? psi[1] - m : 0.0;
+        double d2 = hh[2] != 0.0 ? psi[2] - m : 0.0;
         double w0 = hh[0] * hh[0], w1 = hh[1] * hh[1], w2 = hh[2] * hh[2];
         double qa = (w0 + w1) + w2;
-        double qb = -2.0 * (((w0 * psi[0]) + (w1 * psi[1])) + (w2 * psi[2]));
-        double qc = ((((w0 * psi[0]) * psi[0]) + ((w1 * psi[1]) * psi[1])) +
-                     ((w2 * psi[2]) * psi[2])) - Finv2;
+        double qb = -2.0 * (((w0 * d0) + (w1 * d1)) + (w2 * d2));
+        double qc = ((((w0 * d0) * d0) + ((w1 * d1) * d1)) + ((w2 * d2) * d2)) - Finv2;
         double disc = qb * qb - (4.0 * qa) * qc;
         if (disc >= 0.0) {
-            double t = (-qb + sqrt(disc)) / (2.0 * qa);
-            if (psi[0] < t && psi[1] < t && psi[2] < t) {
+            double u = (-qb + sqrt(disc)) / (2.0 * qa);
+            if (d0 < u && d1 < u && d2 < u) {
+                double t = m + u;
                 if (t < psi_temp) {
                     psi_temp = t;
                     best_set = cur;

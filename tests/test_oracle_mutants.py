@@ -20,11 +20,15 @@ _spec.loader.exec_module(pins)
 MUTANTS = {
     "discriminant_sign": ("double disc = qb * qb - (4.0 * qa) * qc;",
                           "double disc = qb * qb + (4.0 * qa) * qc;"),
-    "dropped_z_term": ("((w2 * psi[2]) * psi[2])) - Finv2;", "0.0) - Finv2;"),
+    "dropped_z_term": ("((w2 * d2) * d2)) - Finv2;", "0.0) - Finv2;"),
     "wrong_axis_neighbour": ("else if (fabs(m->T[qp]) < fabs(m->T[qm]))",
                              "else if (fabs(m->T[qp]) > fabs(m->T[qm]))"),
-    "missing_causality_axis": ("if (psi[0] < t && psi[1] < t && psi[2] < t) {",
-                               "if (psi[0] < t && psi[1] < t) {"),
+    "missing_causality_axis": ("if (d0 < u && d1 < u && d2 < u) {",
+                               "if (d0 < u && d1 < u) {"),
+    "unshifted_quadratic": ("double d0 = hh[0] != 0.0 ? psi[0] - m : 0.0;\n"
+                            "        double d1 = hh[1] != 0.0 ? psi[1] - m : 0.0;\n"
+                            "        double d2 = hh[2] != 0.0 ? psi[2] - m : 0.0;",
+                            "double d0 = psi[0], d1 = psi[1], d2 = psi[2]; m = 0.0;"),
     "drops_smallest_axis": ("if (hh[a] != 0.0 && (j < 0 || psi[a] >= psi[j]))",
                             "if (hh[a] != 0.0 && (j < 0 || psi[a] <= psi[j]))"),
     "h_power": ("hh[a] = 1.0 / m->h;", "hh[a] = 1.0 / (m->h * m->h);"),
@@ -50,6 +54,7 @@ PINS = [
     (pins.test_axis_plane_exact, {}),
     (pins.test_adjoint_finite_differences, {}),
     (pins.test_adjoint_tangent_dot_product, {}),
+    (pins.test_translation_invariance, {}),
 ]
 
 

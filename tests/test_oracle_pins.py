@@ -200,6 +200,22 @@ def test_two_sided_reinit(oracle, seed, shape):
         assert np.all(np.diff(np.abs(T.ravel()[sel])) >= 0)
 
 
+def test_translation_invariance(oracle):
+    """Eq. (2) involves only differences of psi: raising every FIX value by a
+    constant C must raise the whole solution by C.  With C of a few hundred
+    cells the check also rejects a root formula whose rounding grows with
+    |psi| (the unshifted form loses about 3 (psi F/h)^2 ulp)."""
+    shape = (20, 18, 22)
+    h, F, src = _rand_problem(13, shape)
+    T0, G0 = oracle.init_sources(shape, src)
+    r0 = oracle.march(T0, G0, h, speed=F)
+    C = 700.0 * h
+    TC = np.where(G0 == oracle.KNOWN_FIX, C, T0)
+    rC = oracle.march(TC, G0, h, speed=F)
+    diff = np.abs((rC["T"] - C) - r0["T"])
+    assert np.max(diff) <= 1e-13 * (C + np.max(r0["T"])), np.max(diff)
+
+
 def test_planted_mistake_is_caught(oracle):
     """A wrong sign in the discriminant of a 2-D root changes the value the
     residual check sees: the pins above would fail for such an oracle."""

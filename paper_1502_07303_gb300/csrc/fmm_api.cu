@@ -61,7 +61,7 @@ fmm_status cuda_fail(fmm_handle *hd, cudaError_t e, const char *where)
 void free_state(fmm_handle *hd)
 {
     DeviceState &s = hd->st;
-    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.dirty,
+    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.inbox, s.dirty,
                     s.list[0], s.list[1], s.ctrl, hd->d_src};
     for (void *p : ptrs)
         if (p)
@@ -103,11 +103,11 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
     FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
     if (hd->h_ctrl->error & ERR_SPEED)
         return fail(hd, FMM_ERR_INVALID, "speed values must be finite and > 0");
-    // the constant-speed term of the quadratic: 1/F^2 (fp64) or (h/F)^2 (fp32)
+    // the constant-speed term of the shifted quadratic: (h/F)^2
     hd->params.spd_term = 0.0;
     if (!speed) {
         if (hd->cfg.dtype == FMM_F64) {
-            hd->params.spd_term = 1.0 / (speed_const * speed_const);
+            hd->params.spd_term = (hd->params.h * hd->params.h) / (speed_const * speed_const);
         } else {
             const float hf = (float)hd->params.h;
             const float F = (float)speed_const;
@@ -297,6 +297,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     ALLOC(s.bdelta, nb * hd->rsize);
     ALLOC(s.bmin, 2 * nb * hd->rsize);
     ALLOC(s.fresh, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.inbox, nb * kFaces * sizeof(unsigned long long));
     ALLOC(s.dirty, nb * sizeof(unsigned));
     ALLOC(s.list[0], nb * sizeof(int));
     ALLOC(s.list[1], nb * sizeof(int));

@@ -18,7 +18,7 @@ constexpr int kB3 = 512;
 constexpr int kTile = 10;          // brick plus one halo layer per side
 constexpr int kTile3 = 1000;
 constexpr int kFaces = 6;          // -x, +x, -y, +y, -z, +z
-constexpr int kThreads = 512;      // one thread per brick cell
+constexpr int kThreads = 512;      // threads of the per-brick helper kernels
 
 // Cell tag (brick layout).  Bits 0-1: status; bit 2: side -1; bit 3: padding
 // cell beyond the grid.  The status values equal the public fmm_tag values.
@@ -51,6 +51,7 @@ struct Control {
     unsigned int dirty_count;        // count_global: bricks with pending
                                      // overlap changes
     unsigned int n_list[2];          // lengths of the two work lists
+    unsigned int work[2];            // next unclaimed entry of each list
     int done;
     int error;
     int restart;
@@ -70,7 +71,7 @@ struct SolveParams {
     double width;       // width_band
     double stride;      // delta_s (absolute units)
     double bucket;      // bucket width factor
-    double spd_term;    // speed term of a constant speed: 1/F^2 (fp64), (h/F)^2 (fp32)
+    double spd_term;    // speed term (h/F)^2 of a constant speed
     long long max_restarts;
     int max_rounds;     // per brick march
 };
@@ -83,7 +84,8 @@ struct DeviceState {
     void *bdelta;       // per-brick bucket width (h * min slowness / sqrt 3)
     uint8_t *tape;      // upwind set per cell or null
     void *bmin;         // 2 per brick: min |psi| of BAND cells per side
-    unsigned long long *fresh;   // 6 per brick: changed-halo masks
+    unsigned long long *fresh;   // 6 per brick: changed-halo masks (live)
+    unsigned long long *inbox;   // 6 per brick: masks taken by the last selection
     unsigned int *dirty;         // 1 per brick: has pending overlap changes
     int *list[2];       // work lists
     Control *ctrl;

@@ -12,13 +12,14 @@
 //   Collect/Exchange/Integrate (Alg. 13-15) -> write-back to HBM plus per-face
 //                                               "fresh" bit masks and a dirty
 //                                               flag on the neighbour brick; the
-//                                               neighbour's next staging reads
-//                                               the new values
+//                                               select kernel moves the masks to
+//                                               the neighbour's inbox and its next
+//                                               staging reads the new values
 //   second march of Alg. 16                 -> k_march<mode 1> on the bricks
 //                                               made dirty by the first march
 //
-// Inside a brick the heap of Algorithm 12 is replaced by a bucketed,
-// label-correcting march: each round accepts every BAND cell whose |psi| is
+// Inside a brick (one warp per brick) the heap of Algorithm 12 is replaced by
+// a bucketed, label-correcting march: each round accepts every BAND cell whose |psi| is
 // within a bucket width of the brick's BAND minimum (and within the restart
 // bound), then every cell next to a newly accepted cell re-solves Algorithm
 // 11.  A cell whose value drops is reset to BAND even if it was accepted,
@@ -62,138 +63,99 @@ __device__ __forceinline__ void brick_coords(const Geom &g, long long b, int &bx
 //
 // kv holds the value of every KNOWN/FIX cell of the brick and its halo and
 // +inf elsewhere, so "G in KNOWN and |psi_n| < |psi_cell|" is "kv_n < Tc".
-// The per-axis choice and the loop that drops the largest psi_i follow the
-// algorithm; the root of the smallest causal set wins.  set_out receives
-// the upwind set of the returned root (2 bits per axis: 1 = minus, 2 = plus).
+// The per-axis choice and the nested upwind sets (each time dropping the
+// largest psi_i) follow the algorithm.  Algorithm 11 keeps the smallest
+// causal root over the sets; going from the full set down, the first causal
+// root already is that minimum: a causal root t_S of a nested set S satisfies
+// sum over all axes of max(t_S - psi_i, 0)^2 >= (h/F)^2, so t_S is never
+// below the unique solution t* of sum max(t - psi_i, 0)^2 = (h/F)^2, and t*
+// is the causal root of the set {i : psi_i < t*}.  The loop therefore stops
+// at the first causal root.  set_out receives its upwind set (2 bits per
+// axis: 1 = minus, 2 = plus neighbour).
+//
+// |psi| values are never negative, so double comparisons are done on the
+// bit patterns (integer compares keep them off the FP64 pipe).
 // ---------------------------------------------------------------------------
 
-// Double precision: the coefficients a, b, c of Algorithm 11 written with
-// round-to-nearest intrinsics so that no multiply-add is fused.
-__device__ __forceinline__ double solve_cell(const double *kv, int ti, double Tc, double finv2,
-                                             double w, uint8_t &set_out)
+__device__ __forceinline__ bool lt(double a, double b)
 {
-    const int off[3] = {1, kTile, kTile * kTile};
-    double psi[3], wa[3];
-    int nd = 0;
-    unsigned cur = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double vm = kv[ti - off[a]], vp = kv[ti + off[a]];
-        int d = 0;
-        if (vm < Tc)
-            d = -1;
-        if (vp < Tc && (d == 0 || vp < vm))
-            d = 1;
-        psi[a] = d == 0 ? 0.0 : (d < 0 ? vm : vp);
-        wa[a] = d == 0 ? 0.0 : w;
-        if (d != 0) {
-            ++nd;
-            cur |= (d < 0 ? 1u : 2u) << (2 * a);
-        }
-    }
-    double best = inf_v<double>();
-    unsigned best_set = 0;
-#pragma unroll 1
-    while (nd != 0) {
-        const double qa = __dadd_rn(__dadd_rn(wa[0], wa[1]), wa[2]);
-        const double sb = __dadd_rn(__dadd_rn(__dmul_rn(wa[0], psi[0]), __dmul_rn(wa[1], psi[1])),
-                                    __dmul_rn(wa[2], psi[2]));
-        const double qb = -2.0 * sb;
-        const double sc =
-            __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(wa[0], psi[0]), psi[0]),
-                                __dmul_rn(__dmul_rn(wa[1], psi[1]), psi[1])),
-                      __dmul_rn(__dmul_rn(wa[2], psi[2]), psi[2]));
-        const double qc = __dsub_rn(sc, finv2);
-        const double disc = __dsub_rn(__dmul_rn(qb, qb), __dmul_rn(4.0 * qa, qc));
-        if (disc >= 0.0) {
-            const double t = __ddiv_rn(__dadd_rn(-qb, __dsqrt_rn(disc)), 2.0 * qa);
-            if (psi[0] < t && psi[1] < t && psi[2] < t && t < best) {
-                best = t;
-                best_set = cur;
-            }
-        }
-        // drop the axis with the largest psi still in the stencil (ties: the
-        // higher axis index)
-        int j = -1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (wa[a] != 0.0 && (j < 0 || psi[a] >= (j == 0 ? psi[0] : (j == 1 ? psi[1] : psi[2]))))
-                j = a;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == j) {
-                psi[a] = 0.0;
-                wa[a] = 0.0;
-            }
-        cur &= ~(3u << (2 * j));
-        --nd;
-    }
-    set_out = (uint8_t)best_set;
-    return best;
+    // valid for values >= 0 and +inf; a negative discriminant has the sign
+    // bit set and compares below every non-negative value
+    return __double_as_longlong(a) < __double_as_longlong(b);
 }
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ double vmin(double a, double b) { return lt(a, b) ? a : b; }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
-// Single precision: the same algorithm with the unknown shifted by the
-// smallest upwind value (t = m + u, delta_i = psi_i - m, sum (u - delta_i)^2
-// = (h/F)^2), which keeps the quadratic well conditioned when psi >> h.
-__device__ __forceinline__ float solve_cell(const float *kv, int ti, float Tc, float q,
-                                            double /*w*/, uint8_t &set_out)
+__device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
+
+// The quadratic of Algorithm 11, sum_i (t - psi_i)^2 / h^2 = 1/F^2 over the
+// upwind set, is solved for the unknown shifted by the smallest upwind value
+// m: t = m + u, delta_i = psi_i - m, sum_i (u - delta_i)^2 = q with
+// q = (h/F)^2.  The coefficients stay of order h, so rounding does not grow
+// with psi (in psi itself b^2 and 4ac would cancel to ~3 (psi F/h)^2 ulp).
+// The causality test psi_i < t is delta_i < u.  q is the cell's speed term.
+template <typename real>
+__device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real q,
+                                           uint8_t &set_out)
 {
     const int off[3] = {1, kTile, kTile * kTile};
-    float psi[3];
+    real psi[3];
     bool act[3];
     int nd = 0;
     unsigned cur = 0;
-    float m = inf_v<float>();
+    real m = inf_v<real>();
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float vm = kv[ti - off[a]], vp = kv[ti + off[a]];
+        const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
         int d = 0;
-        if (vm < Tc)
+        if (lt(vm, Tc))
             d = -1;
-        if (vp < Tc && (d == 0 || vp < vm))
+        if (lt(vp, Tc) && (d == 0 || lt(vp, vm)))
             d = 1;
         act[a] = d != 0;
-        psi[a] = d == 0 ? 0.f : (d < 0 ? vm : vp);
+        psi[a] = d == 0 ? (real)0 : (d < 0 ? vm : vp);
         if (d != 0) {
             ++nd;
             cur |= (d < 0 ? 1u : 2u) << (2 * a);
-            m = fminf(m, psi[a]);
+            m = vmin(m, psi[a]);
         }
     }
-    float del[3];
+    real del[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-        del[a] = act[a] ? psi[a] - m : 0.f;
-    float best = inf_v<float>();
-    unsigned best_set = 0;
+        del[a] = act[a] ? psi[a] - m : (real)0;
 #pragma unroll 1
-    while (nd != 0) {
-        float S = 0.f, Q = 0.f;
+    for (; nd != 0; --nd) {
+        real S = 0, Q = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             if (act[a]) {
                 S += del[a];
                 Q += del[a] * del[a];
             }
-        const float k = (float)nd;
-        const float disc = S * S - k * (Q - q);
-        if (disc >= 0.f) {
-            const float u = (S + sqrtf(disc)) / k;
+        const real k = (real)nd;
+        const real disc = S * S - k * (Q - q);
+        if (!lt(disc, (real)0)) {
+            const real inv_k = nd == 1 ? (real)1 : (nd == 2 ? (real)0.5 : (real)(1.0 / 3.0));
+            const real u = (S + vsqrt(disc)) * inv_k;
             bool causal = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                causal = causal && (!act[a] || del[a] < u);
-            const float t = m + u;
-            if (causal && t < best) {
-                best = t;
-                best_set = cur;
+                causal = causal && (!act[a] || lt(del[a], u));
+            if (causal) {
+                set_out = (uint8_t)cur;
+                return m + u;
             }
         }
+        // drop the axis with the largest psi still in the stencil (ties: the
+        // higher axis index)
         int j = -1;
-        float dj = 0.f;
+        real dj = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (act[a] && (j < 0 || del[a] >= dj)) {
+            if (act[a] && (j < 0 || !lt(del[a], dj))) {
                 j = a;
                 dj = del[a];
             }
@@ -202,10 +164,9 @@ __device__ __forceinline__ float solve_cell(const float *kv, int ti, float Tc, f
             if (a == j)
                 act[a] = false;
         cur &= ~(3u << (2 * j));
-        --nd;
     }
-    set_out = (uint8_t)best_set;
-    return best;
+    set_out = 0;
+    return inf_v<real>();
 }
 
 template <typename real>
@@ -213,7 +174,7 @@ __device__ __forceinline__ real warp_min(real v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -330,10 +291,9 @@ __global__ void k_init_reinit(Geom g, double h, const real *__restrict__ phi, re
     }
 }
 
-// Speed field to brick layout.  Double precision keeps 1/F^2 (the F^-2 term of
-// Algorithm 11); single precision keeps (h/F)^2 for the shifted solve.  Each
-// brick also records its bucket width h * min(1/F) / sqrt(3).
-__device__ __forceinline__ double speed_term(double F, double h) { return __ddiv_rn(1.0, __dmul_rn(F, F)); }
+// Speed field to brick layout: the speed term (h/F)^2 of the shifted solve.
+// Each brick also records its bucket width h * min(1/F) / sqrt(3).
+__device__ __forceinline__ double speed_term(double F, double h) { return (h * h) / (F * F); }
 __device__ __forceinline__ float speed_term(float F, double h)
 {
     const float hf = (float)h;
@@ -381,30 +341,88 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
 }
 
 // ---------------------------------------------------------------------------
-// The brick march.  kMode 0: Algorithm 9 (relax every non-FIX cell next to a
-// FIX cell once, accept nothing) over all bricks.  kMode 1: Algorithm 12 up to
-// the restart bound over the bricks of work list `which`.
+// The brick march: one warp per brick.  kMode 0: Algorithm 9 over all bricks
+// (every non-FIX cell next to a known cell is solved once, nothing is
+// accepted).  kMode 1: Algorithm 12 up to the restart bound over the bricks
+// of work list `which`.
+//
+// Cell sets of a brick are 512-bit masks held as sixteen 32-bit words; lane k
+// (k < 16) holds word k, which covers the cells 32k .. 32k+31, i.e. z = k/2,
+// y = 4(k%2) .. 4(k%2)+3, all x (bit = x + 8 (y % 4)).  The cells to solve in
+// a round are compacted into a list so that all 32 lanes do useful work.
 // ---------------------------------------------------------------------------
 
+constexpr int kMarchWarps = 4;   // bricks in flight per CTA
+constexpr unsigned FULL = 0xffffffffu;
+
 template <typename real>
-struct MarchShared {
-    real kv[kTile3];
-    real red[2][kThreads / 32];
-    unsigned int facebits[kFaces][2];
-    unsigned int outbits[kFaces][2];
-    uint8_t acc[kB3];
+struct WarpTile {
+    real kv[kTile3];      // known values of the brick and its face halo
+    real tv[kB3];         // current |psi| of the brick's cells
+    uint8_t tg[kB3];      // tags
+    uint8_t tp[kB3];      // upwind sets (tape)
+    uint16_t list[kB3];   // compacted cells to solve
 };
 
-__device__ __forceinline__ bool face_bit(const unsigned (*bits)[2], int f, int q)
+__device__ __forceinline__ int tile_of(int c)
 {
-    return (bits[f][q >> 5] >> (q & 31)) & 1u;
+    return 111 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
+}
+
+// Cells of word k (lane k) next to a cell of the 512-bit set A (same layout).
+__device__ __forceinline__ unsigned neighbour_words(unsigned A, int lane)
+{
+    const unsigned Ap1 = __shfl_down_sync(FULL, A, 1);
+    const unsigned Am1 = __shfl_up_sync(FULL, A, 1);
+    const unsigned Ap2 = __shfl_down_sync(FULL, A, 2);
+    const unsigned Am2 = __shfl_up_sync(FULL, A, 2);
+    unsigned r = ((A << 1) & 0xFEFEFEFEu) | ((A >> 1) & 0x7F7F7F7Fu);   // x -/+ 1
+    r |= (A << 8) | (A >> 8);                                            // y inside the word
+    if (lane & 1)
+        r |= Am1 >> 24;                                                  // y = 3 -> y = 4
+    else
+        r |= Ap1 << 24;                                                  // y = 4 -> y = 3
+    if (lane >= 2)
+        r |= Am2;                                                        // z - 1
+    if (lane + 2 < 16)
+        r |= Ap2;                                                        // z + 1
+    return lane < 16 ? r : 0u;
+}
+
+// Cells of word k next to a halo cell flagged in the per-face masks F[6]
+// (face bit = u + 8 v with (u, v) the two in-face coordinates).
+__device__ __forceinline__ unsigned face_words(const unsigned long long F[kFaces], int k)
+{
+    if (k >= 16)
+        return 0u;
+    const int z = k >> 1, y0 = 4 * (k & 1);
+    unsigned r = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int bit = y0 + j + 8 * z;
+        if ((F[0] >> bit) & 1ull)
+            r |= 1u << (8 * j);
+        if ((F[1] >> bit) & 1ull)
+            r |= 1u << (8 * j + 7);
+    }
+    if ((k & 1) == 0)
+        r |= (unsigned)((F[2] >> (8 * z)) & 0xFFull);
+    else
+        r |= (unsigned)((F[3] >> (8 * z)) & 0xFFull) << 24;
+    if (k < 2)
+        r |= (unsigned)(F[4] >> (32 * (k & 1)));
+    if (k >= 14)
+        r |= (unsigned)(F[5] >> (32 * (k & 1)));
+    return r;
 }
 
 template <typename real, bool kHetero, int kMode>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kMarchWarps * 32)
     k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
 {
-    __shared__ MarchShared<real> sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
     if (kMode == 1 && ctrl->done)
         return;
@@ -414,45 +432,51 @@ __global__ void __launch_bounds__(kThreads, 2)
     const real *spd = (const real *)s.spd;
     const real *bdelta = (const real *)s.bdelta;
     real *bmin = (real *)s.bmin;
-    const int t = threadIdx.x;
-    const int x = t & 7, y = (t >> 3) & 7, z = t >> 6;
-    const int ti = (x + 1) + kTile * (y + 1) + kTile * kTile * (z + 1);
     const real INF = inf_v<real>();
     const real bound0 = (real)ctrl->bound[0], bound1 = (real)ctrl->bound[1];
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    unsigned long long st_marches = 0, st_rounds = 0, st_acc = 0, st_exch = 0;
 
-    for (long long it = blockIdx.x; it < n; it += gridDim.x) {
+    // bricks of the work list are taken one at a time from a shared counter
+    // (the next index is fetched while the current brick is processed)
+    long long it = 0, next = 0;
+    if (kMode == 1) {
+        if (lane == 0) {
+            it = (long long)atomicAdd(&ctrl->work[which], 1u);
+            next = (long long)atomicAdd(&ctrl->work[which], 1u);
+        }
+        it = __shfl_sync(FULL, it, 0);
+        next = __shfl_sync(FULL, next, 0);
+    } else {
+        it = (long long)blockIdx.x * kMarchWarps + warp;
+    }
+    while (it < n) {
         const long long b = (kMode == 0) ? it : (long long)s.list[which][it];
         int bx, by, bz;
         brick_coords(g, b, bx, by, bz);
         const long long base = b * kB3;
 
-        // ---- stage the brick (owned: plain loads) -------------------------
-        real tv = T[base + t];
-        uint8_t tg = tag[base + t];
-        const real sp = kHetero ? spd[base + t] : (real)spd_const_term;
-        uint8_t tp = s.tape ? s.tape[base + t] : (uint8_t)0;
-        const real kv0 = is_known(tg) ? tv : INF;
-        sh.kv[ti] = kv0;
-        if (t < 2 * kFaces)
-            (&sh.outbits[0][0])[t] = 0u;
-        if (kMode == 1 && t == 0) {
-            // consume the pending-change flag and masks before reading the
-            // halo: a change flagged after this point marks the brick again
-            atomicExch(&s.dirty[b], 0u);
-            __threadfence();
-#pragma unroll
-            for (int f = 0; f < kFaces; ++f) {
-                const unsigned long long m = atomicExch(&s.fresh[b * kFaces + f], 0ull);
-                sh.facebits[f][0] = (unsigned)m;
-                sh.facebits[f][1] = (unsigned)(m >> 32);
-            }
-            __threadfence();
+        // ---- stage the brick (owned by this warp: plain loads) ------------
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+            const int c = lane + 32 * k;
+            const real v = T[base + c];
+            const uint8_t t = tag[base + c];
+            W.tv[c] = v;
+            W.tg[c] = t;
+            W.kv[tile_of(c)] = is_known(t) ? v : INF;
+            if (s.tape)
+                W.tp[c] = s.tape[base + c];
         }
-        __syncthreads();
-
-        // ---- halo: the neighbour bricks' boundary layers (read-only) -------
-        if (t < kFaces * 64) {
-            const int f = t >> 6, q = t & 63, u = q & 7, v = q >> 3;
+        // ---- halo: the face layers of the six neighbours (read-only) ------
+        unsigned long long F[kFaces];
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            F[f] = 0ull;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const int h = lane + 32 * k;
+            const int f = h >> 6, q = h & 63, u = q & 7, v = q >> 3;
             const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
             const int nbx = bx + (axis == 0 ? dir : 0);
             const int nby = by + (axis == 1 ? dir : 0);
@@ -474,137 +498,212 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int hx = axis == 0 ? hedge : u + 1;
             const int hy = axis == 1 ? hedge : (axis == 0 ? u + 1 : v + 1);
             const int hz = axis == 2 ? hedge : v + 1;
-            sh.kv[hx + kTile * hy + kTile * kTile * hz] = val;
-        }
-        __syncthreads();
-
-        const bool frozen = ((tg & ST_MASK) == ST_FIX) || (tg & TG_OUT);
-        const bool neg = (tg & TG_NEG) != 0;
-        bool relax = false;
-        if (!frozen) {
+            W.kv[hx + kTile * hy + kTile * kTile * hz] = val;
             if (kMode == 0) {
-                relax = sh.kv[ti - 1] < tv || sh.kv[ti + 1] < tv || sh.kv[ti - kTile] < tv ||
-                        sh.kv[ti + kTile] < tv || sh.kv[ti - kTile * kTile] < tv ||
-                        sh.kv[ti + kTile * kTile] < tv;
-            } else {
-                const unsigned(*fb)[2] = sh.facebits;
-                if (x == 0 && face_bit(fb, 0, y + 8 * z) && sh.kv[ti - 1] < tv) relax = true;
-                if (x == 7 && face_bit(fb, 1, y + 8 * z) && sh.kv[ti + 1] < tv) relax = true;
-                if (y == 0 && face_bit(fb, 2, x + 8 * z) && sh.kv[ti - kTile] < tv) relax = true;
-                if (y == 7 && face_bit(fb, 3, x + 8 * z) && sh.kv[ti + kTile] < tv) relax = true;
-                if (z == 0 && face_bit(fb, 4, x + 8 * y) && sh.kv[ti - kTile * kTile] < tv) relax = true;
-                if (z == 7 && face_bit(fb, 5, x + 8 * y) && sh.kv[ti + kTile * kTile] < tv) relax = true;
+                // Algorithm 9: every known halo cell updates its neighbours
+                const unsigned bal = __ballot_sync(FULL, lt(val, INF));
+                F[k >> 1] |= (unsigned long long)bal << (32 * (k & 1));
             }
         }
+        if (kMode == 1) {
+            // changed halo cells, snapshotted by the select kernel
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f)
+                F[f] = s.inbox[b * kFaces + f];
+        }
+        __syncwarp();
+
+        // ---- masks: frozen (FIX or padding) and known cells ----------------
+        unsigned frozen_w = 0, known_w = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint8_t t = W.tg[lane + 32 * k];
+            const unsigned fz = __ballot_sync(FULL, ((t & ST_MASK) == ST_FIX) || (t & TG_OUT));
+            const unsigned kn = __ballot_sync(FULL, is_known(t));
+            if (lane == k) {
+                frozen_w = fz;
+                known_w = kn;
+            }
+        }
+        unsigned relax_w = face_words(F, lane);
+        if (kMode == 0)
+            relax_w |= neighbour_words(known_w, lane);
+        relax_w &= ~frozen_w;
 
         const real delta = (real)p.bucket * bdelta[b];
+        unsigned acc_any_w = 0;
         int rounds = 0;
-        long long n_acc = 0;
         real m0 = INF, m1 = INF;
         for (;;) {
-            // Algorithm 10/11: re-solve next to the newly accepted cells
-            real cand = INF;
-            uint8_t cset = 0;
-            if (relax)
-                cand = solve_cell(sh.kv, ti, tv, sp, p.w, cset);
-            __syncthreads();
-            if (cand < tv) {
-                tv = cand;
-                tg = (uint8_t)((tg & ~ST_MASK) | ST_BAND);
-                sh.kv[ti] = INF;
-                tp = cset;
+            // compact the cells to solve
+            int n_items = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const unsigned word = __shfl_sync(FULL, relax_w, k);
+                if ((word >> lane) & 1u)
+                    W.list[n_items + __popc(word & lanemask_lt)] = (uint16_t)(32 * k + lane);
+                n_items += __popc(word);
+            }
+            __syncwarp();
+            // Algorithm 10/11: solve, then apply (Jacobi within 32 cells)
+            for (int i0 = 0; i0 < n_items; i0 += 32) {
+                const int i = i0 + lane;
+                int c = -1;
+                real cand = INF;
+                uint8_t cset = 0;
+                if (i < n_items) {
+                    c = W.list[i];
+                    const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
+                    cand = solve_cell<real>(W.kv, tile_of(c), W.tv[c], sp, cset);
+                }
+                __syncwarp();
+                if (c >= 0 && lt(cand, W.tv[c])) {
+                    W.tv[c] = cand;
+                    W.tg[c] = (uint8_t)((W.tg[c] & ~ST_MASK) | ST_BAND);
+                    W.kv[tile_of(c)] = INF;
+                    W.tp[c] = cset;
+                }
+                __syncwarp();
             }
             // minimum of the BAND cells of each side (the heap tops)
-            const bool band = (tg & ST_MASK) == ST_BAND;
-            real b0 = warp_min<real>(band && neg ? tv : INF);
-            real b1 = warp_min<real>(band && !neg ? tv : INF);
-            if ((t & 31) == 0) {
-                sh.red[0][t >> 5] = b0;
-                sh.red[1][t >> 5] = b1;
-            }
-            __syncthreads();
-            m0 = sh.red[0][0];
-            m1 = sh.red[1][0];
+            real l0 = INF, l1 = INF;
 #pragma unroll
-            for (int w = 1; w < kThreads / 32; ++w) {
-                m0 = fmin(m0, sh.red[0][w]);
-                m1 = fmin(m1, sh.red[1][w]);
+            for (int k = 0; k < 16; ++k) {
+                const int c = lane + 32 * k;
+                const uint8_t t = W.tg[c];
+                if ((t & ST_MASK) == ST_BAND) {
+                    const real v = W.tv[c];
+                    if (t & TG_NEG)
+                        l0 = vmin(l0, v);
+                    else
+                        l1 = vmin(l1, v);
+                }
             }
+            m0 = warp_min(l0);
+            m1 = warp_min(l1);
             if (kMode == 0)
                 break;
             // accept the lowest bucket up to the restart bound
-            const real lim = neg ? fmin(m0 + delta, bound0) : fmin(m1 + delta, bound1);
-            const bool acc = band && tv <= lim;
-            if (acc) {
-                tg = (uint8_t)((tg & ~ST_MASK) | ST_KNOWN);
-                sh.kv[ti] = tv;
+            const real lim0 = vmin(m0 + delta, bound0), lim1 = vmin(m1 + delta, bound1);
+            unsigned acc_w = 0;
+            int nacc = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int c = lane + 32 * k;
+                const uint8_t t = W.tg[c];
+                bool a = false;
+                if ((t & ST_MASK) == ST_BAND) {
+                    const real v = W.tv[c];
+                    a = !lt((t & TG_NEG) ? lim0 : lim1, v);
+                    if (a) {
+                        W.tg[c] = (uint8_t)((t & ~ST_MASK) | ST_KNOWN);
+                        W.kv[tile_of(c)] = v;
+                    }
+                }
+                const unsigned bw = __ballot_sync(FULL, a);
+                if (lane == k)
+                    acc_w = bw;
+                nacc += __popc(bw);
             }
-            sh.acc[t] = acc;
-            const int na = __syncthreads_count(acc);
-            if (na == 0)
+            if (nacc == 0)
                 break;
-            n_acc += na;
+            acc_any_w |= acc_w;
+            st_acc += (unsigned long long)nacc;
             if (++rounds > p.max_rounds) {
-                if (t == 0)
+                if (lane == 0)
                     atomicOr(&ctrl->error, ERR_ROUNDS);
                 break;
             }
-            relax = false;
-            if (!frozen) {
-                if (x > 0 && sh.acc[t - 1] && sh.kv[ti - 1] < tv) relax = true;
-                if (x < 7 && sh.acc[t + 1] && sh.kv[ti + 1] < tv) relax = true;
-                if (y > 0 && sh.acc[t - 8] && sh.kv[ti - kTile] < tv) relax = true;
-                if (y < 7 && sh.acc[t + 8] && sh.kv[ti + kTile] < tv) relax = true;
-                if (z > 0 && sh.acc[t - 64] && sh.kv[ti - kTile * kTile] < tv) relax = true;
-                if (z < 7 && sh.acc[t + 64] && sh.kv[ti + kTile * kTile] < tv) relax = true;
-            }
+            __syncwarp();
+            relax_w = neighbour_words(acc_w, lane) & ~frozen_w;
         }
 
         // ---- write back, front minima, overlap change notification --------
-        T[base + t] = tv;
-        tag[base + t] = tg;
-        if (s.tape)
-            s.tape[base + t] = tp;
-        if (t == 0) {
+        // A boundary cell accepted here (and known at the end) is flagged to
+        // the neighbour only if the adjacent halo cell is not known with a
+        // value at or below it: such a neighbour cell can never take it as an
+        // upwind value (Algorithm 11 uses only smaller known neighbours, and
+        // values only decrease), so the exchange would change nothing there.
+        unsigned long long fo0 = 0, fo1 = 0, fo2 = 0, fo3 = 0, fo4 = 0, fo5 = 0;
+        const int x = lane & 7, yl = (lane >> 3) & 3;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int c = lane + 32 * k;
+            const uint8_t t = W.tg[c];
+            const real v = W.tv[c];
+            T[base + c] = v;
+            tag[base + c] = t;
+            if (s.tape)
+                s.tape[base + c] = W.tp[c];
+            if (kMode == 1) {
+                const unsigned acc_word = __shfl_sync(FULL, acc_any_w, k);
+                if (((acc_word >> lane) & 1u) && is_known(t)) {
+                    const int y = yl + 4 * (k & 1), z = k >> 1;
+                    const int ti = tile_of(c);
+                    if (x == 0 && lt(v, W.kv[ti - 1]))
+                        fo0 |= 1ull << (y + 8 * z);
+                    if (x == 7 && lt(v, W.kv[ti + 1]))
+                        fo1 |= 1ull << (y + 8 * z);
+                    if (y == 0 && lt(v, W.kv[ti - kTile]))
+                        fo2 |= 1ull << (x + 8 * z);
+                    if (y == 7 && lt(v, W.kv[ti + kTile]))
+                        fo3 |= 1ull << (x + 8 * z);
+                    if (z == 0 && lt(v, W.kv[ti - kTile * kTile]))
+                        fo4 |= 1ull << (x + 8 * y);
+                    if (z == 7 && lt(v, W.kv[ti + kTile * kTile]))
+                        fo5 |= 1ull << (x + 8 * y);
+                }
+            }
+        }
+        if (lane == 0) {
             bmin[2 * b] = m0;
             bmin[2 * b + 1] = m1;
         }
         if (kMode == 1) {
-            const real kvf = is_known(tg) ? tv : INF;
-            if (kvf < kv0) {
-                unsigned(*ob)[2] = sh.outbits;
-                if (x == 0) atomicOr(&ob[0][(y + 8 * z) >> 5], 1u << ((y + 8 * z) & 31));
-                if (x == 7) atomicOr(&ob[1][(y + 8 * z) >> 5], 1u << ((y + 8 * z) & 31));
-                if (y == 0) atomicOr(&ob[2][(x + 8 * z) >> 5], 1u << ((x + 8 * z) & 31));
-                if (y == 7) atomicOr(&ob[3][(x + 8 * z) >> 5], 1u << ((x + 8 * z) & 31));
-                if (z == 0) atomicOr(&ob[4][(x + 8 * y) >> 5], 1u << ((x + 8 * y) & 31));
-                if (z == 7) atomicOr(&ob[5][(x + 8 * y) >> 5], 1u << ((x + 8 * y) & 31));
+            unsigned long long out[kFaces] = {fo0, fo1, fo2, fo3, fo4, fo5};
+            unsigned long long m = 0;
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f) {
+                const unsigned lo = __reduce_or_sync(FULL, (unsigned)out[f]);
+                const unsigned hi = __reduce_or_sync(FULL, (unsigned)(out[f] >> 32));
+                if (lane == f)
+                    m = (unsigned long long)lo | ((unsigned long long)hi << 32);
             }
-            __threadfence();
-            __syncthreads();
-            if (t < kFaces) {
-                const int f = t;
-                const unsigned long long m =
-                    (unsigned long long)sh.outbits[f][0] | ((unsigned long long)sh.outbits[f][1] << 32);
+            if (lane < kFaces && m) {
+                const int f = lane;
                 const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
                 const int nbx = bx + (axis == 0 ? dir : 0);
                 const int nby = by + (axis == 1 ? dir : 0);
                 const int nbz = bz + (axis == 2 ? dir : 0);
-                if (m && nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 &&
-                    nbz < g.nbz) {
+                if (nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 && nbz < g.nbz) {
                     const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
                     atomicOr(&s.fresh[nb * kFaces + (f ^ 1)], m);
-                    atomicExch(&s.dirty[nb], 1u);
-                    atomicAdd(&ctrl->exchanges, (unsigned long long)__popcll(m));
+                    s.dirty[nb] = 1u;
+                    st_exch += (unsigned long long)__popcll(m);
                 }
             }
-            if (t == 0) {
-                atomicAdd(&ctrl->marches, 1ull);
-                atomicAdd(&ctrl->rounds, (unsigned long long)rounds);
-                atomicAdd(&ctrl->accepted, (unsigned long long)n_acc);
-            }
+            st_marches += 1;
+            st_rounds += (unsigned long long)rounds;
         }
-        __syncthreads();
+        __syncwarp();
+        // next brick (dynamic scheduling)
+        if (kMode == 1) {
+            it = next;
+            if (it < n && lane == 0)
+                next = (long long)atomicAdd(&ctrl->work[which], 1u) + 0;
+            next = __shfl_sync(FULL, next, 0);
+        } else {
+            it += (long long)gridDim.x * kMarchWarps;
+        }
+    }
+    if (kMode == 1) {
+        st_exch = __reduce_add_sync(FULL, (unsigned)st_exch);
+        if (lane == 0 && st_marches) {
+            atomicAdd(&ctrl->marches, st_marches);
+            atomicAdd(&ctrl->rounds, st_rounds);
+            atomicAdd(&ctrl->accepted, st_acc);
+            atomicAdd(&ctrl->exchanges, st_exch);
+        }
     }
 }
 
@@ -675,14 +774,20 @@ __global__ void k_control(Control *c, double width, double stride, long long max
     c->dirty_count = 0u;
     c->n_list[0] = 0u;
     c->n_list[1] = 0u;
+    c->work[0] = 0u;
+    c->work[1] = 0u;
 }
 
 // Work lists: list 0 = bricks with a BAND cell at or below the bound or with
 // pending overlap changes (first march); list 1 = bricks with pending changes
-// (second march, after the exchange).
+// (second march, after the exchange).  A selected brick's change masks are
+// moved to its inbox here, between kernels, so the march reads them without
+// atomics; changes flagged during the march accumulate in the live masks for
+// the next selection.
 template <typename real>
-__global__ void k_select(Geom g, const real *__restrict__ bmin, const unsigned *__restrict__ dirty,
-                         Control *ctrl, int *list, int which)
+__global__ void k_select(Geom g, const real *__restrict__ bmin, unsigned *dirty,
+                         unsigned long long *fresh, unsigned long long *inbox, Control *ctrl,
+                         int *list, int which)
 {
     if (ctrl->done)
         return;
@@ -691,11 +796,22 @@ __global__ void k_select(Geom g, const real *__restrict__ bmin, const unsigned *
     for (long long b0 = blockIdx.x * (long long)blockDim.x; b0 < g.nbricks;
          b0 += (long long)gridDim.x * blockDim.x) {
         const long long b = b0 + threadIdx.x;
-        bool sel = false;
+        bool sel = false, dty = false;
         if (b < g.nbricks) {
-            sel = dirty[b] != 0u;
+            dty = dirty[b] != 0u;
+            sel = dty;
             if (which == 0)
                 sel = sel || (double)bmin[2 * b] <= bd0 || (double)bmin[2 * b + 1] <= bd1;
+        }
+        if (sel) {
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f) {
+                inbox[b * kFaces + f] = dty ? fresh[b * kFaces + f] : 0ull;
+                if (dty)
+                    fresh[b * kFaces + f] = 0ull;
+            }
+            if (dty)
+                dirty[b] = 0u;
         }
         const unsigned ball = __ballot_sync(0xffffffffu, sel);
         if (ball == 0u)
@@ -718,6 +834,7 @@ __global__ void k_reset_control(Control *c)
     c->bound[0] = c->bound[1] = 0.0;
     c->dirty_count = 0u;
     c->n_list[0] = c->n_list[1] = 0u;
+    c->work[0] = c->work[1] = 0u;
     c->done = 0;
     c->error = 0;
     c->restart = 0;
@@ -761,27 +878,58 @@ int grid_for(long long n, int threads, int cap)
 }
 
 template <typename real>
+size_t march_smem() { return sizeof(WarpTile<real>) * kMarchWarps; }
+
+template <typename real>
 cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
                          cudaStream_t st, cudaEvent_t *ev4)
 {
     const int rb = grid_for(g.nbricks, 256, 4096);
     const bool het = s.spd != nullptr;
     const double sct = p.spd_term;
+    const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
     for (int which = 0; which < 2; ++which) {
-        k_select<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl,
-                                           s.list[which], which);
+        k_select<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.fresh, s.inbox,
+                                           s.ctrl, s.list[which], which);
         if (ev4)
             cudaEventRecord(ev4[2 * which], st);
         if (het)
-            k_march<real, true, 1><<<s.march_ctas, kThreads, 0, st>>>(g, s, p, sct, which);
+            k_march<real, true, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
         else
-            k_march<real, false, 1><<<s.march_ctas, kThreads, 0, st>>>(g, s, p, sct, which);
+            k_march<real, false, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
         if (ev4)
             cudaEventRecord(ev4[2 * which + 1], st);
     }
     return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t front_init_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
+                            cudaStream_t st)
+{
+    const long long need = (g.nbricks + kMarchWarps - 1) / kMarchWarps;
+    const int nb = (int)(need < s.march_ctas ? need : s.march_ctas);
+    const size_t sm = march_smem<real>();
+    if (s.spd)
+        k_march<real, true, 0><<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
+    else
+        k_march<real, false, 0><<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
+    return cudaGetLastError();
+}
+
+template <typename real>
+int configure_march()
+{
+    const int sm = (int)march_smem<real>();
+    cudaFuncSetAttribute(k_march<real, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march<real, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march<real, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march<real, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1>, kMarchWarps * 32, sm);
+    return n > 0 ? n : 1;
 }
 
 }  // namespace
@@ -835,20 +983,7 @@ cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s, do
 cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
                               const SolveParams &p, cudaStream_t st)
 {
-    const bool het = s.spd != nullptr;
-    const int nb = (int)(g.nbricks < s.march_ctas ? g.nbricks : s.march_ctas);
-    if (dtype == 1) {
-        if (het)
-            k_march<double, true, 0><<<nb, kThreads, 0, st>>>(g, s, p, p.spd_term, 0);
-        else
-            k_march<double, false, 0><<<nb, kThreads, 0, st>>>(g, s, p, p.spd_term, 0);
-    } else {
-        if (het)
-            k_march<float, true, 0><<<nb, kThreads, 0, st>>>(g, s, p, p.spd_term, 0);
-        else
-            k_march<float, false, 0><<<nb, kThreads, 0, st>>>(g, s, p, p.spd_term, 0);
-    }
-    return cudaGetLastError();
+    return dtype == 1 ? front_init_impl<double>(g, s, p, st) : front_init_impl<float>(g, s, p, st);
 }
 
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
@@ -877,12 +1012,7 @@ cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s, void *
 
 int march_blocks_per_sm(int dtype)
 {
-    int n = 0;
-    if (dtype == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<double, true, 1>, kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<float, true, 1>, kThreads, 0);
-    return n > 0 ? n : 1;
+    return dtype == 1 ? configure_march<double>() : configure_march<float>();
 }
 
 }  // namespace fmmgb

@@ -47,7 +47,8 @@ constexpr size_t kOffTag = align256(kOffT + kCells * sizeof(double));
 constexpr size_t kOffBdelta = align256(kOffTag + kCells);
 constexpr size_t kOffBmin = align256(kOffBdelta + kNoAllocMaxBricks * sizeof(double));
 constexpr size_t kOffFresh = align256(kOffBmin + 2 * kNoAllocMaxBricks * sizeof(double));
-constexpr size_t kOffDirty = align256(kOffFresh + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
+constexpr size_t kOffInbox = align256(kOffFresh + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
+constexpr size_t kOffDirty = align256(kOffInbox + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
 constexpr size_t kOffList0 = align256(kOffDirty + kNoAllocMaxBricks * sizeof(unsigned));
 constexpr size_t kOffList1 = align256(kOffList0 + kNoAllocMaxBricks * sizeof(int));
 constexpr size_t kOffCtrl = align256(kOffList1 + kNoAllocMaxBricks * sizeof(int));
@@ -142,6 +143,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     s.bdelta = base + kOffBdelta;
     s.bmin = base + kOffBmin;
     s.fresh = (unsigned long long *)(base + kOffFresh);
+    s.inbox = (unsigned long long *)(base + kOffInbox);
     s.dirty = (unsigned *)(base + kOffDirty);
     s.list[0] = (int *)(base + kOffList0);
     s.list[1] = (int *)(base + kOffList1);
@@ -162,7 +164,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     if (cfg->dtype == FMM_F64) {
-        p.spd_term = 1.0;   // 1/F^2 with F = 1
+        p.spd_term = cfg->h * cfg->h;   // (h/F)^2 with F = 1
     } else {
         const float hf = (float)cfg->h;
         p.spd_term = (double)(hf * hf);   // (h/F)^2 with F = 1

@@ -4,7 +4,7 @@
 Workload (one "step" = one complete solve through the C ABI): two-sided
 signed-distance reinitialisation of 32 seeded random spheres with the
 sin-modulated level set on a 256^3 unit cube (16.8 M points), fp32, full
-march, stride 2h.  The metric is grid points finalised per second (Gpoints/s).
+march, the library's default restart parameters.  The metric is grid points finalised per second (Gpoints/s).
 fp64 is measured on the same workload and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -342,7 +342,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"reinit random_spheres{N_SPHERES} {n}^3", "grid": [n, n, n],
-                   "points_per_gpu": pts, "seed": SEED, "stride_h": 2.0, "bucket": 1.0,
+                   "points_per_gpu": pts, "seed": SEED,
+                   "restart_params": "library defaults (fp32: stride 16h, bucket 4, 2 exchange "
+                                     "passes; fp64: stride 8h, bucket 4, 1 pass)",
                    "brick": 8, "l2": "flushed before every step (256 MiB write)",
                    "replicas": ws, "parallelism": "independent replicas, no collective"},
         "roofline": roofline(r32, "f32"),

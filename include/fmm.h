@@ -62,10 +62,12 @@ typedef struct {
     int32_t record_tape;   /* 1: keep the upwind sets for fmm_adjoint           */
     double width;          /* width_band (Algorithm 5/12); 0 -> +inf (full march) */
     double stride;         /* restart stride delta_s in units of h (Algorithm 16);
-                              0 -> 2 (the paper's suggestion, Sec. 5.5);
+                              0 -> the GB300 default (16 for FMM_F32, 8 for
+                              FMM_F64; the paper suggests 2 for its CPU
+                              cluster and tuning per platform, Sec. 5.5);
                               +inf allowed                                     */
     double bucket;         /* accepted bucket width inside a brick, in units of
-                              h * min(1/F) / sqrt(3); 0 -> 1; +inf allowed     */
+                              h * min(1/F) / sqrt(3); 0 -> 4; +inf allowed     */
     int32_t ctas;          /* CTAs of the march kernel; 0 -> as many as fit     */
     int32_t timeout_s;     /* host wall-clock limit of one solve in seconds;
                               0 -> 600; exceeding it returns FMM_ERR_TIMEOUT  */
@@ -73,7 +75,9 @@ typedef struct {
     void *stream;          /* cudaStream_t                                      */
     int32_t time_kernels;  /* 1: time every march launch with CUDA events on
                               the solve's stream (fmm_stats.march_ms)         */
-    int32_t reserved1;
+    int32_t exchange_passes; /* exchange + march passes after the first march
+                              of every restart (Algorithm 16 has 1); 0 -> the
+                              GB300 default (2 for FMM_F32, 1 for FMM_F64)   */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */

@@ -141,19 +141,20 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     bool timed_out = false;
     long long batch = 1;
     for (;;) {
+        const size_t ev_per = 2 * (size_t)(1 + hd->params.passes);
         for (long long r = 0; r < batch; ++r) {
-            cudaEvent_t *ev4 = nullptr;
+            cudaEvent_t *ev = nullptr;
             if (timing) {
-                while (hd->events.size() < ev_used + 4) {
+                while (hd->events.size() < ev_used + ev_per) {
                     cudaEvent_t e;
                     FMM_CUDA(hd, cudaEventCreate(&e));
                     hd->events.push_back(e);
                 }
-                ev4 = &hd->events[ev_used];
-                ev_used += 4;
+                ev = &hd->events[ev_used];
+                ev_used += ev_per;
             }
-            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st, ev4));
-            launches += kLaunchesPerRestart;
+            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st, ev));
+            launches += launches_per_restart(hd->params.passes);
         }
         FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
         FMM_CUDA(hd, cudaStreamSynchronize(st));
@@ -181,8 +182,8 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     }
     FMM_CUDA(hd, cudaStreamSynchronize(st));
     // restarts after the terminating pass only return; the march launches
-    // that did work are the two of every pass but the last
-    const long long worked = c.restart > 0 ? 2LL * (c.restart - 1) : 0;
+    // that did work are those of every pass but the last
+    const long long worked = c.restart > 0 ? (1LL + hd->params.passes) * (c.restart - 1) : 0;
     hd->stats.march_launches = worked;
     hd->stats.kernel_launches = launches + hd->pre_launches;
     hd->pre_launches = 0;
@@ -236,6 +237,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
         cfg->bucket < 0.0 || std::isnan(cfg->bucket))
         return fail(nullptr, FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
+    if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
+        return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
     if (n_src < 0 || (n_src > 0 && !src_ijk))
         return fail(nullptr, FMM_ERR_INVALID, "bad source list");
     if (speed && !aligned16(speed))
@@ -266,9 +269,10 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     const double hh = 1.0 / cfg->h;
     p.w = hh * hh;
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
-    const double stride_h = cfg->stride > 0.0 ? cfg->stride : 2.0;
+    const double stride_h = cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype);
     p.stride = stride_h * cfg->h;
-    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : 1.0;
+    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
+    p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
 

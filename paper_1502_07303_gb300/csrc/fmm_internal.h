@@ -74,7 +74,14 @@ struct SolveParams {
     double spd_term;    // speed term (h/F)^2 of a constant speed
     long long max_restarts;
     int max_rounds;     // per brick march
+    int passes;         // exchange + march passes after the first march
 };
+
+// Defaults of the restart parameters (units of h and of the bucket width),
+// measured on GB300 for 8^3 bricks.
+inline double default_stride(int dtype) { return dtype == 1 ? 8.0 : 16.0; }
+inline int default_passes(int dtype) { return dtype == 1 ? 1 : 2; }
+constexpr double kDefaultBucket = 4.0;
 
 // Device buffers owned by a handle (typed by the launchers).
 struct DeviceState {
@@ -105,12 +112,13 @@ cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s,
                               cudaStream_t stream);
 cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
                               const SolveParams &p, cudaStream_t stream);
-// One pass of the Algorithm 16 loop: reduce, control, and the two
-// select + march phases (6 launches).  ev4, when not null, holds two event
-// pairs recorded around the two march launches.
-constexpr int kLaunchesPerRestart = 6;
+// One pass of the Algorithm 16 loop: reduce, control, the first select +
+// march, then p.passes exchange passes (select + march, with a list reset
+// before every pass but the first).  ev, when not null, holds one event pair
+// per march launch (2 * (1 + passes) events).
+inline int launches_per_restart(int passes) { return 2 + 2 * (1 + passes) + (passes - 1); }
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
-                           const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev4);
+                           const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev);
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);

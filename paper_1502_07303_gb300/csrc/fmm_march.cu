@@ -87,7 +87,19 @@ __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ double vmin(double a, double b) { return lt(a, b) ? a : b; }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
-__device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
+// Double square root: the single-precision reciprocal square root refined by
+// one Newton step in double (relative error about 1e-13, far below the
+// solver's tolerance; it keeps most of the work off the FP64 pipe).  Values
+// outside the float range take the library square root.
+__device__ __forceinline__ double vsqrt(double v)
+{
+    const float vf = (float)v;
+    if (!(vf >= 1e-30f && vf <= 1e30f))
+        return sqrt(v);
+    const double r = (double)rsqrtf(vf);
+    const double y = v * r;
+    return fma(0.5 * r, fma(-y, y, v), y);
+}
 __device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
 
 // The quadratic of Algorithm 11, sum_i (t - psi_i)^2 / h^2 = 1/F^2 over the
@@ -880,9 +892,17 @@ int grid_for(long long n, int threads, int cap)
 template <typename real>
 size_t march_smem() { return sizeof(WarpTile<real>) * kMarchWarps; }
 
+__global__ void k_reset_list(Control *c, int which)
+{
+    if (c->done)
+        return;
+    c->n_list[which] = 0u;
+    c->work[which] = 0u;
+}
+
 template <typename real>
 cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
-                         cudaStream_t st, cudaEvent_t *ev4)
+                         cudaStream_t st, cudaEvent_t *ev)
 {
     const int rb = grid_for(g.nbricks, 256, 4096);
     const bool het = s.spd != nullptr;
@@ -890,17 +910,20 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
-    for (int which = 0; which < 2; ++which) {
+    for (int pass = 0; pass <= p.passes; ++pass) {
+        const int which = pass == 0 ? 0 : 1;
+        if (pass >= 2)
+            k_reset_list<<<1, 1, 0, st>>>(s.ctrl, 1);
         k_select<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.fresh, s.inbox,
                                            s.ctrl, s.list[which], which);
-        if (ev4)
-            cudaEventRecord(ev4[2 * which], st);
+        if (ev)
+            cudaEventRecord(ev[2 * pass], st);
         if (het)
             k_march<real, true, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
         else
             k_march<real, false, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
-        if (ev4)
-            cudaEventRecord(ev4[2 * which + 1], st);
+        if (ev)
+            cudaEventRecord(ev[2 * pass + 1], st);
     }
     return cudaGetLastError();
 }
@@ -987,9 +1010,9 @@ cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
 }
 
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
-                           cudaStream_t st, cudaEvent_t *ev4)
+                           cudaStream_t st, cudaEvent_t *ev)
 {
-    return dtype == 1 ? restart_impl<double>(g, s, p, st, ev4) : restart_impl<float>(g, s, p, st, ev4);
+    return dtype == 1 ? restart_impl<double>(g, s, p, st, ev) : restart_impl<float>(g, s, p, st, ev);
 }
 
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st)

@@ -159,8 +159,11 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     const double hh = 1.0 / cfg->h;
     p.w = hh * hh;
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
-    p.stride = (cfg->stride > 0.0 ? cfg->stride : 2.0) * cfg->h;
-    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : 1.0;
+    p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * cfg->h;
+    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
+    p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
+    if (p.passes > 64)
+        return error(FMM_ERR_INVALID, "exchange_passes must be at most 64");
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     if (cfg->dtype == FMM_F64) {

@@ -31,7 +31,7 @@ class FmmConfig(ctypes.Structure):
                 ("stride", ctypes.c_double), ("bucket", ctypes.c_double),
                 ("ctas", ctypes.c_int32), ("timeout_s", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p),
-                ("time_kernels", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
@@ -120,8 +120,9 @@ class Solver:
     sources (i, j, k)."""
 
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
-                 width=math.inf, stride=2.0, bucket=1.0, record_tape=False, ctas=0,
-                 max_restarts=0, timeout_s=0, time_kernels=False, stream=None):
+                 width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
+                 max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
+                 stream=None):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
@@ -139,6 +140,7 @@ class Solver:
         cfg.max_restarts = int(max_restarts)
         cfg.timeout_s = int(timeout_s)
         cfg.time_kernels = 1 if time_kernels else 0
+        cfg.exchange_passes = int(exchange_passes)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)
@@ -240,7 +242,7 @@ def reinit(phi0, h, dtype=None, **kw):
         return T, G, s.stats()
 
 
-def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=2.0, bucket=1.0,
+def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=0.0, bucket=0.0,
                    stream=None):
     """Reinitialisation (F = 1) through fmm_reinit_signed_distance_noalloc,
     for callers that cannot allocate device memory: the library allocates

@@ -29,6 +29,8 @@ struct fmm_handle {
     long long pre_launches = 0;       // init launches of the current solve
     fmm_stats stats;
     std::vector<cudaEvent_t> events;   // march timing pairs (time_kernels)
+    void *adj_mu = nullptr;            // adjoint workspace (lambda / D per cell)
+    unsigned *adj_count = nullptr;
     std::string err;
 };
 
@@ -71,6 +73,12 @@ void free_state(fmm_handle *hd)
     for (cudaEvent_t e : hd->events)
         cudaEventDestroy(e);
     hd->events.clear();
+    if (hd->adj_mu)
+        cudaFree(hd->adj_mu);
+    if (hd->adj_count)
+        cudaFree(hd->adj_count);
+    hd->adj_mu = nullptr;
+    hd->adj_count = nullptr;
     memset(&hd->st, 0, sizeof(hd->st));
     hd->d_src = nullptr;
     hd->h_ctrl = nullptr;
@@ -370,7 +378,57 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
         return fail(hd, FMM_ERR_INVALID, "dL_dT and dL_dslowness must be device pointers");
     if (!hd->solved || !hd->tape_valid)
         return fail(hd, FMM_ERR_STATE, "fmm_adjoint needs a solve with record_tape = 1 first");
-    return fail(hd, FMM_ERR_STATE, "adjoint kernel not available in this build");
+    if (!aligned16(dL_dT) || !aligned16(dL_dslowness))
+        return fail(hd, FMM_ERR_INVALID, "dL_dT and dL_dslowness must be 16-byte aligned");
+    const Geom &g = hd->geom;
+    DeviceState &s = hd->st;
+    cudaStream_t st = hd->stream;
+    const int dt = hd->cfg.dtype;
+    if (!hd->adj_mu)
+        FMM_CUDA(hd, alloc(&hd->adj_mu, (size_t)g.nbricks * kB3 * hd->rsize));
+    if (!hd->adj_count)
+        FMM_CUDA(hd, alloc(&hd->adj_count, sizeof(unsigned)));
+    AdjointArgs a;
+    a.dLdT = dL_dT;
+    a.dlds = dL_dslowness;
+    a.mu = hd->adj_mu;
+    a.h = hd->params.h;
+    a.spd_term = hd->params.spd_term;
+    // every cell becomes ready once its downwind neighbours have published;
+    // bricks run again while a neighbour finished cells they depend on
+    FMM_CUDA(hd, launch_reset_control(s, st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
+    FMM_CUDA(hd, launch_adjoint_march(dt, g, s, a, 0, 1, st));
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit_s = hd->cfg.timeout_s > 0 ? (double)hd->cfg.timeout_s : 600.0;
+    long long batch = 1, iters = 0;
+    for (;;) {
+        for (long long r = 0; r < batch; ++r) {
+            FMM_CUDA(hd, launch_reset_list(s, 1, st));
+            FMM_CUDA(hd, launch_select(dt, g, s, 1, st));
+            FMM_CUDA(hd, launch_adjoint_march(dt, g, s, a, 1, 1, st));
+        }
+        iters += batch;
+        FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA(hd, cudaStreamSynchronize(st));
+        if (hd->h_ctrl->n_list[1] == 0)
+            break;
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s)
+            return fail(hd, FMM_ERR_TIMEOUT, "the adjoint exceeded its wall-clock limit (timeout_s)");
+        if (batch < 16)
+            batch *= 2;
+    }
+    FMM_CUDA(hd, cudaMemsetAsync(hd->adj_count, 0, sizeof(unsigned), st));
+    FMM_CUDA(hd, launch_adjoint_pending(dt, g, a, hd->adj_count, st));
+    unsigned left = 0;
+    FMM_CUDA(hd, cudaMemcpyAsync(&left, hd->adj_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    hd->stats.adjoint_iterations = iters;
+    if (left != 0)
+        return fail(hd, FMM_ERR_STATE, "adjoint: some accepted cells could not be ordered");
+    return FMM_OK;
 }
 
 fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out)

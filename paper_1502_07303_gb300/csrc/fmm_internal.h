@@ -123,5 +123,25 @@ cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);
 int march_blocks_per_sm(int dtype);
+cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int which,
+                          cudaStream_t stream);
+cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t stream);
+
+// Adjoint (fmm_adjoint.cu).
+struct AdjointArgs {
+    const void *dLdT;   // caller's dL/dpsi, x-fastest
+    void *dlds;         // caller's dL/ds output, x-fastest
+    void *mu;           // lambda / D per cell (brick layout), NaN until done
+    double h;
+    double spd_term;    // (h/F)^2 of a constant speed
+};
+cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
+                                const AdjointArgs &a, cudaStream_t stream);
+// mode 0: every brick; mode 1: the bricks of work list `which`
+cudaError_t launch_adjoint_march(int dtype, const Geom &g, const DeviceState &s,
+                                 const AdjointArgs &a, int mode, int which,
+                                 cudaStream_t stream);
+cudaError_t launch_adjoint_pending(int dtype, const Geom &g, const AdjointArgs &a,
+                                   unsigned *count, cudaStream_t stream);
 
 }  // namespace fmmgb

@@ -1033,6 +1033,25 @@ cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s, void *
     return cudaGetLastError();
 }
 
+cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int which,
+                          cudaStream_t st)
+{
+    const int rb = grid_for(g.nbricks, 256, 4096);
+    if (dtype == 1)
+        k_select<double><<<rb, 256, 0, st>>>(g, (const double *)s.bmin, s.dirty, s.fresh, s.inbox,
+                                             s.ctrl, s.list[which], which);
+    else
+        k_select<float><<<rb, 256, 0, st>>>(g, (const float *)s.bmin, s.dirty, s.fresh, s.inbox,
+                                            s.ctrl, s.list[which], which);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t st)
+{
+    k_reset_list<<<1, 1, 0, st>>>(s.ctrl, which);
+    return cudaGetLastError();
+}
+
 int march_blocks_per_sm(int dtype)
 {
     return dtype == 1 ? configure_march<double>() : configure_march<float>();

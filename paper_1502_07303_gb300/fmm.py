@@ -39,7 +39,7 @@ class FmmStats(ctypes.Structure):
                 ("march_rounds", ctypes.c_int64), ("exchanges", ctypes.c_int64),
                 ("accepted", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("march_launches", ctypes.c_int64),
-                ("march_ms", ctypes.c_double),
+                ("march_ms", ctypes.c_double), ("adjoint_iterations", ctypes.c_int64),
                 ("error_flags", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
     def as_dict(self):

@@ -154,6 +154,33 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
  */
 fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness);
 
+/*
+ * fmm_create_batch -- a solver for n_grids independent grids of uneven sizes
+ * that are reinitialised together (speed F = 1): the bricks of all grids are
+ * packed into one brick array and every phase of the restart loop of
+ * Algorithm 16 is one launch over one shared work list; no data crosses from
+ * one grid to another.  The restart bound is common to all grids (Algorithm
+ * 16 is correct for any bound; a grid whose front is done simply has no work).
+ *   dims : host, 3 * n_grids int64 (nx, ny, nz of every grid)
+ *   h    : host, n_grids spacings
+ *   cfg  : dtype, width, stride (in units of the smallest h), bucket,
+ *          exchange_passes, ctas, max_restarts, timeout_s, time_kernels,
+ *          stream; nx, ny, nz, h and record_tape are ignored / must be 0.
+ * The batch handle works with fmm_reinit_batch, fmm_get_stats,
+ * fmm_last_error and fmm_destroy.  (Batching is not part of the paper.)
+ */
+fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
+                            const fmm_config *cfg, fmm_handle **out);
+
+/*
+ * fmm_reinit_batch -- two-sided reinitialisation of every grid of a batch
+ * handle (the per-grid rule of fmm_reinit_signed_distance).  phi0, T_out
+ * (and tags_out, which may be NULL or hold NULL entries) are host arrays of
+ * n_grids device pointers to each grid's x-fastest arrays of the dtype.
+ */
+fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const *T_out,
+                            uint8_t *const *tags_out);
+
 /* fmm_get_stats -- statistics of the last solve (synchronises the stream). */
 fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out);
 

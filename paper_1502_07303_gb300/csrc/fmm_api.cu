@@ -31,6 +31,12 @@ struct fmm_handle {
     std::vector<cudaEvent_t> events;   // march timing pairs (time_kernels)
     void *adj_mu = nullptr;            // adjoint workspace (lambda / D per cell)
     unsigned *adj_count = nullptr;
+    // batches (fmm_create_batch)
+    int n_grids = 0;
+    BatchGrid *d_grids = nullptr;
+    BatchGrid *h_grids = nullptr;      // pinned
+    int *d_bgrid = nullptr;
+    int *d_nbr = nullptr;
     std::string err;
 };
 
@@ -73,6 +79,18 @@ void free_state(fmm_handle *hd)
     for (cudaEvent_t e : hd->events)
         cudaEventDestroy(e);
     hd->events.clear();
+    if (hd->d_grids)
+        cudaFree(hd->d_grids);
+    if (hd->d_bgrid)
+        cudaFree(hd->d_bgrid);
+    if (hd->d_nbr)
+        cudaFree(hd->d_nbr);
+    if (hd->h_grids)
+        cudaFreeHost(hd->h_grids);
+    hd->d_grids = nullptr;
+    hd->d_bgrid = nullptr;
+    hd->d_nbr = nullptr;
+    hd->h_grids = nullptr;
     if (hd->adj_mu)
         cudaFree(hd->adj_mu);
     if (hd->adj_count)
@@ -351,6 +369,8 @@ fmm_status fmm_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (!T_out || !aligned16(T_out))
         return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "a batch handle solves with fmm_reinit_batch");
     FMM_CUDA(hd, launch_init_sources(hd->cfg.dtype, hd->geom, hd->st, hd->d_src, hd->n_src, hd->stream));
     hd->pre_launches = hd->n_src > 0 ? 2 : 1;
     return run_solve(hd, T_out, tags_out);
@@ -365,6 +385,8 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
         return fail(hd, FMM_ERR_INVALID, "phi0 must be a 16-byte aligned device pointer");
     if (!T_out || !aligned16(T_out))
         return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "a batch handle solves with fmm_reinit_batch");
     FMM_CUDA(hd, launch_init_reinit(hd->cfg.dtype, hd->geom, hd->st, hd->params, phi0, hd->stream));
     hd->pre_launches = 1;
     return run_solve(hd, T_out, tags_out);
@@ -428,6 +450,181 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     hd->stats.adjoint_iterations = iters;
     if (left != 0)
         return fail(hd, FMM_ERR_STATE, "adjoint: some accepted cells could not be ordered");
+    return FMM_OK;
+}
+
+fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
+                            const fmm_config *cfg, fmm_handle **out)
+{
+    if (!out)
+        return fail(nullptr, FMM_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    if (!cfg || !dims || !h || n_grids < 1)
+        return fail(nullptr, FMM_ERR_INVALID, "need n_grids >= 1, dims, h and cfg");
+    if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
+        return fail(nullptr, FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
+    if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
+        cfg->bucket < 0.0 || std::isnan(cfg->bucket) || cfg->exchange_passes < 0 ||
+        cfg->exchange_passes > 64)
+        return fail(nullptr, FMM_ERR_INVALID, "bad width, stride, bucket or exchange_passes");
+    if (cfg->record_tape)
+        return fail(nullptr, FMM_ERR_INVALID, "batches keep no tape (record_tape must be 0)");
+    std::vector<BatchGrid> grids((size_t)n_grids);
+    long long total = 0;
+    double hmin = INFINITY;
+    for (int gi = 0; gi < n_grids; ++gi) {
+        const int64_t nx = dims[3 * gi], ny = dims[3 * gi + 1], nz = dims[3 * gi + 2];
+        if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+            return fail(nullptr, FMM_ERR_INVALID, "grid sizes must be in [1, 2^20]");
+        if (!(h[gi] > 0.0) || !std::isfinite(h[gi]))
+            return fail(nullptr, FMM_ERR_INVALID, "every h must be finite and > 0");
+        BatchGrid &G = grids[gi];
+        memset(&G, 0, sizeof(G));
+        G.nx = (int)nx;
+        G.ny = (int)ny;
+        G.nz = (int)nz;
+        G.nbx = (G.nx + kB - 1) / kB;
+        G.nby = (G.ny + kB - 1) / kB;
+        G.nbz = (G.nz + kB - 1) / kB;
+        G.brick0 = total;
+        G.h = h[gi];
+        total += (long long)G.nbx * G.nby * G.nbz;
+        hmin = h[gi] < hmin ? h[gi] : hmin;
+    }
+    if (total >= (1LL << 31))
+        return fail(nullptr, FMM_ERR_INVALID, "too many bricks in one batch");
+    // grid of every brick and the neighbour table (no neighbour across grids)
+    std::vector<int> bgrid((size_t)total), nbr((size_t)total * kFaces);
+    for (int gi = 0; gi < n_grids; ++gi) {
+        const BatchGrid &G = grids[gi];
+        for (int bz = 0; bz < G.nbz; ++bz)
+            for (int by = 0; by < G.nby; ++by)
+                for (int bx = 0; bx < G.nbx; ++bx) {
+                    const long long b = G.brick0 + ((long long)bz * G.nby + by) * G.nbx + bx;
+                    bgrid[(size_t)b] = gi;
+                    const int c[3] = {bx, by, bz}, e[3] = {G.nbx, G.nby, G.nbz};
+                    for (int f = 0; f < kFaces; ++f) {
+                        const int a = f >> 1, d = (f & 1) ? 1 : -1;
+                        int q[3] = {bx, by, bz};
+                        q[a] += d;
+                        nbr[(size_t)b * kFaces + f] =
+                            (q[a] < 0 || q[a] >= e[a])
+                                ? -1
+                                : (int)(G.brick0 + ((long long)q[2] * G.nby + q[1]) * G.nbx + q[0]);
+                        (void)c;
+                    }
+                }
+    }
+    fmm_handle *hd = new (std::nothrow) fmm_handle();
+    if (!hd)
+        return fail(nullptr, FMM_ERR_OOM, "host allocation failed");
+    hd->cfg = *cfg;
+    hd->stream = (cudaStream_t)cfg->stream;
+    hd->rsize = cfg->dtype == FMM_F64 ? 8 : 4;
+    hd->n_grids = n_grids;
+    memset(&hd->stats, 0, sizeof(hd->stats));
+    memset(&hd->st, 0, sizeof(hd->st));
+    Geom &g = hd->geom;
+    memset(&g, 0, sizeof(g));
+    g.nbricks = total;
+    SolveParams &p = hd->params;
+    p.h = hmin;
+    p.w = (1.0 / hmin) * (1.0 / hmin);
+    p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
+    p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * hmin;
+    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
+    p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
+    p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
+    p.max_rounds = 1 << 22;
+    p.spd_term = 0.0;
+    auto bail = [&](fmm_status code) {
+        g_create_error = hd->err;
+        free_state(hd);
+        delete hd;
+        return code;
+    };
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return bail(cuda_fail(hd, e, "cudaGetDevice"));
+    DeviceState &s = hd->st;
+    const size_t nb = (size_t)total, cells = nb * kB3;
+#define ALLOC(ptr, bytes)                                          \
+    do {                                                           \
+        cudaError_t e2 = alloc(&(ptr), (bytes));                   \
+        if (e2 != cudaSuccess)                                     \
+            return bail(cuda_fail(hd, e2, "cudaMalloc " #ptr));     \
+    } while (0)
+    ALLOC(s.T, cells * hd->rsize);
+    ALLOC(s.tag, cells);
+    ALLOC(s.spd, cells * hd->rsize);
+    ALLOC(s.bdelta, nb * hd->rsize);
+    ALLOC(s.bmin, 2 * nb * hd->rsize);
+    ALLOC(s.fresh, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.inbox, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.dirty, nb * sizeof(unsigned));
+    ALLOC(s.list[0], nb * sizeof(int));
+    ALLOC(s.list[1], nb * sizeof(int));
+    ALLOC(s.ctrl, sizeof(Control));
+    ALLOC(hd->d_nbr, nb * kFaces * sizeof(int));
+    ALLOC(hd->d_bgrid, nb * sizeof(int));
+    ALLOC(hd->d_grids, (size_t)n_grids * sizeof(BatchGrid));
+#undef ALLOC
+    e = cudaMallocHost((void **)&hd->h_ctrl, sizeof(Control));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&hd->h_grids, (size_t)n_grids * sizeof(BatchGrid));
+    if (e != cudaSuccess)
+        return bail(cuda_fail(hd, e, "cudaMallocHost"));
+    memcpy(hd->h_grids, grids.data(), (size_t)n_grids * sizeof(BatchGrid));
+    s.nbr = hd->d_nbr;
+    const int per_sm = march_blocks_per_sm(cfg->dtype);
+    s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
+    e = cudaMemcpy(hd->d_nbr, nbr.data(), nb * kFaces * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hd->d_bgrid, bgrid.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hd->d_grids, hd->h_grids, (size_t)n_grids * sizeof(BatchGrid),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_batch_speed(cfg->dtype, hd->d_grids, hd->d_bgrid, total, s, hd->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(hd->stream);
+    if (e != cudaSuccess)
+        return bail(cuda_fail(hd, e, "batch set-up"));
+    *out = hd;
+    return FMM_OK;
+}
+
+fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const *T_out,
+                            uint8_t *const *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "fmm_reinit_batch needs a handle from fmm_create_batch");
+    if (!phi0 || !T_out)
+        return fail(hd, FMM_ERR_INVALID, "phi0 and T_out must be arrays of device pointers");
+    for (int gi = 0; gi < hd->n_grids; ++gi) {
+        if (!phi0[gi] || !aligned16(phi0[gi]) || !T_out[gi] || !aligned16(T_out[gi]))
+            return fail(hd, FMM_ERR_INVALID, "every phi0 and T_out must be 16-byte aligned");
+        hd->h_grids[gi].phi0 = phi0[gi];
+        hd->h_grids[gi].T_out = T_out[gi];
+        hd->h_grids[gi].tags_out = tags_out ? tags_out[gi] : nullptr;
+    }
+    cudaStream_t st = hd->stream;
+    const long long nb = hd->geom.nbricks;
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->d_grids, hd->h_grids, (size_t)hd->n_grids * sizeof(BatchGrid),
+                                 cudaMemcpyHostToDevice, st));
+    FMM_CUDA(hd, launch_batch_init(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
+    hd->pre_launches = 1;
+    fmm_status rc = run_solve(hd, nullptr, nullptr);
+    if (rc != FMM_OK)
+        return rc;
+    FMM_CUDA(hd, launch_batch_output(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    hd->stats.kernel_launches += 1;
     return FMM_OK;
 }
 

@@ -95,8 +95,20 @@ struct DeviceState {
     unsigned long long *inbox;   // 6 per brick: masks taken by the last selection
     unsigned int *dirty;         // 1 per brick: has pending overlap changes
     int *list[2];       // work lists
+    const int *nbr;     // 6 per brick: neighbour brick or -1 (batches only)
     Control *ctrl;
     int march_ctas;
+};
+
+// One grid of a batch (device table).
+struct BatchGrid {
+    int nx, ny, nz;
+    int nbx, nby, nbz;
+    long long brick0;      // first brick of the grid in the packed brick array
+    double h;
+    const void *phi0;      // caller's level set (x-fastest)
+    void *T_out;           // caller's output psi (x-fastest)
+    uint8_t *tags_out;     // caller's output tags or null
 };
 
 // Launchers (fmm_march.cu).  All enqueue on `stream`; `dtype` is 0 for float
@@ -123,6 +135,12 @@ cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);
 int march_blocks_per_sm(int dtype);
+cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgrid,
+                              long long nbricks, const DeviceState &s, cudaStream_t stream);
+cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,
+                               long long nbricks, const DeviceState &s, cudaStream_t stream);
+cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bgrid,
+                                long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int which,
                           cudaStream_t stream);
 cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t stream);

@@ -58,6 +58,25 @@ __device__ __forceinline__ void brick_coords(const Geom &g, long long b, int &bx
     bz = (int)(r / g.nby);
 }
 
+// Brick across face f (0..5 = -x, +x, -y, +y, -z, +z) of brick b, or -1.  A
+// batch of grids stores a neighbour table (no neighbour across the border of
+// a grid); a single grid computes it from the brick coordinates.
+__device__ __forceinline__ long long neighbour_brick(const Geom &g, const int *nbr, long long b,
+                                                    int f)
+{
+    if (nbr)
+        return (long long)nbr[b * kFaces + f];
+    int bx, by, bz;
+    brick_coords(g, b, bx, by, bz);
+    const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
+    const int nbx = bx + (axis == 0 ? dir : 0);
+    const int nby = by + (axis == 1 ? dir : 0);
+    const int nbz = bz + (axis == 2 ? dir : 0);
+    if (nbx < 0 || nbx >= g.nbx || nby < 0 || nby >= g.nby || nbz < 0 || nbz >= g.nbz)
+        return -1;
+    return ((long long)nbz * g.nby + nby) * g.nbx + nbx;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 11 (Solve_Quadratic_Parallel) on a staged tile.
 //
@@ -240,12 +259,62 @@ __device__ __forceinline__ float crossing(float fc, float fq, double h)
     return (fc / (fc - fq)) * (float)h;
 }
 
+// Algorithm 8 for one cell (i, j, k) of an nx*ny*nz level set.
+template <typename real>
+__device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx, int ny, int nz,
+                                            int i, int j, int k, double h, real &Tv, uint8_t &tg)
+{
+    const long long sx = 1, sy = nx, sz = (long long)nx * ny;
+    const long long p = (long long)k * sz + (long long)j * sy + i;
+    const real fc = phi[p];
+    const bool pos = fc >= (real)0;
+    real d[3];
+    bool any = false;
+    const int co[3] = {i, j, k};
+    const int ext[3] = {nx, ny, nz};
+    const long long st[3] = {sx, sy, sz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = inf_v<real>();
+#pragma unroll
+        for (int dir = -1; dir <= 1; dir += 2) {
+            const int q = co[a] + dir;
+            if (q < 0 || q >= ext[a])
+                continue;
+            const real fq = phi[p + dir * st[a]];
+            if ((fq >= (real)0) == pos)
+                continue;
+            const real dist = crossing(fc, fq, h);
+            if (dist < d[a])
+                d[a] = dist;
+            any = true;
+        }
+    }
+    if (!any) {
+        Tv = inf_v<real>();
+        tg = pos ? (uint8_t)ST_FAR : (uint8_t)(ST_FAR | TG_NEG);
+        return;
+    }
+    real inv = (real)0;
+    bool zero = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == inf_v<real>())
+            continue;
+        if (d[a] == (real)0)
+            zero = true;
+        else
+            inv = inv + rcp_sq(d[a]);
+    }
+    Tv = zero ? (real)0 : inv_sqrt_exact(inv);
+    tg = pos ? (uint8_t)ST_FIX : (uint8_t)(ST_FIX | TG_NEG);
+}
+
 template <typename real>
 __global__ void k_init_reinit(Geom g, double h, const real *__restrict__ phi, real *T,
                               uint8_t *tag)
 {
     const long long n = g.nbricks * kB3;
-    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         int bx, by, bz;
@@ -257,49 +326,11 @@ __global__ void k_init_reinit(Geom g, double h, const real *__restrict__ phi, re
             tag[e] = TG_OUT | ST_FAR;
             continue;
         }
-        const long long p = (long long)k * sz + (long long)j * sy + i;
-        const real fc = phi[p];
-        const bool pos = fc >= (real)0;
-        real d[3];
-        bool any = false;
-        const int co[3] = {i, j, k};
-        const int ext[3] = {g.nx, g.ny, g.nz};
-        const long long st[3] = {sx, sy, sz};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            d[a] = inf_v<real>();
-#pragma unroll
-            for (int dir = -1; dir <= 1; dir += 2) {
-                const int q = co[a] + dir;
-                if (q < 0 || q >= ext[a])
-                    continue;
-                const real fq = phi[p + dir * st[a]];
-                if ((fq >= (real)0) == pos)
-                    continue;
-                const real dist = crossing(fc, fq, h);
-                if (dist < d[a])
-                    d[a] = dist;
-                any = true;
-            }
-        }
-        if (!any) {
-            T[e] = inf_v<real>();
-            tag[e] = pos ? (uint8_t)ST_FAR : (uint8_t)(ST_FAR | TG_NEG);
-            continue;
-        }
-        real inv = (real)0;
-        bool zero = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (d[a] == inf_v<real>())
-                continue;
-            if (d[a] == (real)0)
-                zero = true;
-            else
-                inv = inv + rcp_sq(d[a]);
-        }
-        T[e] = zero ? (real)0 : inv_sqrt_exact(inv);
-        tag[e] = pos ? (uint8_t)ST_FIX : (uint8_t)(ST_FIX | TG_NEG);
+        real Tv;
+        uint8_t tg;
+        reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, h, Tv, tg);
+        T[e] = Tv;
+        tag[e] = tg;
     }
 }
 
@@ -464,8 +495,10 @@ __global__ void __launch_bounds__(kMarchWarps * 32)
     }
     while (it < n) {
         const long long b = (kMode == 0) ? it : (long long)s.list[which][it];
-        int bx, by, bz;
-        brick_coords(g, b, bx, by, bz);
+        long long nbi[kFaces];
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            nbi[f] = neighbour_brick(g, s.nbr, b, f);
         const long long base = b * kB3;
 
         // ---- stage the brick (owned by this warp: plain loads) ------------
@@ -490,16 +523,13 @@ __global__ void __launch_bounds__(kMarchWarps * 32)
             const int h = lane + 32 * k;
             const int f = h >> 6, q = h & 63, u = q & 7, v = q >> 3;
             const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
-            const int nbx = bx + (axis == 0 ? dir : 0);
-            const int nby = by + (axis == 1 ? dir : 0);
-            const int nbz = bz + (axis == 2 ? dir : 0);
             real val = INF;
-            if (nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 && nbz < g.nbz) {
+            const long long nb = nbi[k >> 1];
+            if (nb >= 0) {
                 const int edge = dir < 0 ? kB - 1 : 0;
                 const int cx = axis == 0 ? edge : u;
                 const int cy = axis == 1 ? edge : (axis == 0 ? u : v);
                 const int cz = axis == 2 ? edge : v;
-                const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
                 const long long ci = nb * kB3 + cx + kB * cy + kB * kB * cz;
                 const uint8_t ntg = __ldcg(tag + ci);
                 const real nv = __ldcg(T + ci);
@@ -681,14 +711,15 @@ __global__ void __launch_bounds__(kMarchWarps * 32)
                 if (lane == f)
                     m = (unsigned long long)lo | ((unsigned long long)hi << 32);
             }
+            long long nbl = -1;
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f)
+                if (lane == f)
+                    nbl = nbi[f];
             if (lane < kFaces && m) {
                 const int f = lane;
-                const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
-                const int nbx = bx + (axis == 0 ? dir : 0);
-                const int nby = by + (axis == 1 ? dir : 0);
-                const int nbz = bz + (axis == 2 ? dir : 0);
-                if (nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 && nbz < g.nbz) {
-                    const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
+                if (nbl >= 0) {
+                    const long long nb = nbl;
                     atomicOr(&s.fresh[nb * kFaces + (f ^ 1)], m);
                     s.dirty[nb] = 1u;
                     st_exch += (unsigned long long)__popcll(m);
@@ -879,6 +910,95 @@ __global__ void k_output(Geom g, const real *__restrict__ T, const uint8_t *__re
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batches: the bricks of many grids packed into one brick array.  bgrid[b] is
+// the grid of brick b; the grid table gives its size, first brick, spacing
+// and the caller's arrays.  The neighbour table (DeviceState::nbr) has no
+// neighbour across the border of a grid, so the grids never exchange data.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void batch_cell(const BatchGrid &G, long long b, int c, int &i, int &j,
+                                           int &k)
+{
+    const long long lb = b - G.brick0;
+    const int bx = (int)(lb % G.nbx);
+    const long long r = lb / G.nbx;
+    const int by = (int)(r % G.nby), bz = (int)(r / G.nby);
+    i = bx * kB + (c & 7);
+    j = by * kB + ((c >> 3) & 7);
+    k = bz * kB + (c >> 6);
+}
+
+template <typename real>
+__global__ void k_batch_init_reinit(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
+                                    long long nbricks, real *T, uint8_t *tag)
+{
+    const long long n = nbricks * kB3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e >> 9;
+        const BatchGrid &G = grids[bgrid[b]];
+        int i, j, k;
+        batch_cell(G, b, (int)(e & 511), i, j, k);
+        if (i >= G.nx || j >= G.ny || k >= G.nz) {
+            T[e] = inf_v<real>();
+            tag[e] = TG_OUT | ST_FAR;
+            continue;
+        }
+        real Tv;
+        uint8_t tg;
+        reinit_cell<real>((const real *)G.phi0, G.nx, G.ny, G.nz, i, j, k, G.h, Tv, tg);
+        T[e] = Tv;
+        tag[e] = tg;
+    }
+}
+
+// Speed term (h_g/F)^2 with F = 1 per cell (every grid has its own h) and the
+// bucket width h_g / sqrt(3) per brick.
+template <typename real>
+__global__ void k_batch_speed(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
+                              long long nbricks, real *spd, real *bdelta)
+{
+    const long long n = nbricks * kB3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e >> 9;
+        const double h = grids[bgrid[b]].h;
+        spd[e] = speed_term((real)1, h);
+        if ((e & 511) == 0)
+            bdelta[b] = (real)(h / 1.7320508075688772);
+    }
+}
+
+template <typename real>
+__global__ void k_batch_output(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
+                               long long nbricks, const real *__restrict__ T,
+                               const uint8_t *__restrict__ tag)
+{
+    const long long n = nbricks * kB3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e >> 9;
+        const BatchGrid &G = grids[bgrid[b]];
+        int i, j, k;
+        batch_cell(G, b, (int)(e & 511), i, j, k);
+        if (i >= G.nx || j >= G.ny || k >= G.nz)
+            continue;
+        const long long p = ((long long)k * G.ny + j) * G.nx + i;
+        const real v = T[e];
+        const uint8_t tg = tag[e];
+        const uint8_t st = tg & ST_MASK;
+        real out = v;
+        if (st == ST_FAR)
+            out = inf_v<real>();
+        else if (tg & TG_NEG)
+            out = -v;
+        ((real *)G.T_out)[p] = out;
+        if (G.tags_out)
+            G.tags_out[p] = st;
+    }
+}
+
 int grid_for(long long n, int threads, int cap)
 {
     long long b = (n + threads - 1) / threads;
@@ -1049,6 +1169,41 @@ cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int wh
 cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t st)
 {
     k_reset_list<<<1, 1, 0, st>>>(s.ctrl, which);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgrid,
+                              long long nbricks, const DeviceState &s, cudaStream_t st)
+{
+    const int nb = grid_for(nbricks * kB3, 256, 152 * 32);
+    if (dtype == 1)
+        k_batch_init_reinit<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (double *)s.T, s.tag);
+    else
+        k_batch_init_reinit<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (float *)s.T, s.tag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,
+                               long long nbricks, const DeviceState &s, cudaStream_t st)
+{
+    const int nb = grid_for(nbricks * kB3, 256, 152 * 32);
+    if (dtype == 1)
+        k_batch_speed<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (double *)s.spd,
+                                                  (double *)s.bdelta);
+    else
+        k_batch_speed<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (float *)s.spd,
+                                                 (float *)s.bdelta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bgrid,
+                                long long nbricks, const DeviceState &s, cudaStream_t st)
+{
+    const int nb = grid_for(nbricks * kB3, 256, 152 * 32);
+    if (dtype == 1)
+        k_batch_output<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (const double *)s.T, s.tag);
+    else
+        k_batch_output<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (const float *)s.T, s.tag);
     return cudaGetLastError();
 }
 

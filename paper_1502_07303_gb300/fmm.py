@@ -21,7 +21,7 @@ TAG_FAR, TAG_BAND, TAG_KNOWN, TAG_FIX = 0, 1, 2, 3
 
 EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
-            "fmm_reinit_signed_distance_noalloc")
+            "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch")
 
 
 class FmmConfig(ctypes.Structure):
@@ -81,8 +81,12 @@ def load(path: str | None = None):
     lib.fmm_destroy.argtypes = [vp]
     lib.fmm_destroy.restype = None
     lib.fmm_reinit_signed_distance_noalloc.argtypes = [ctypes.POINTER(FmmConfig), vp, vp, vp]
+    lib.fmm_create_batch.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(FmmConfig),
+                                     ctypes.POINTER(vp)]
+    lib.fmm_reinit_batch.argtypes = [vp, vp, vp, vp]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
-              "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc"):
+              "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
+              "fmm_create_batch", "fmm_reinit_batch"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -240,6 +244,86 @@ def reinit(phi0, h, dtype=None, **kw):
     with Solver(tuple(phi0.shape), h, dtype=dtype, **kw) as s:
         T, G = s.reinit(phi0.to(dtype).contiguous())
         return T, G, s.stats()
+
+
+class Batch:
+    """Many independent grids (shapes (nz, ny, nx) with spacings hs)
+    reinitialised together by fmm_create_batch / fmm_reinit_batch."""
+
+    def __init__(self, shapes, hs, dtype=torch.float32, width=math.inf, stride=0.0, bucket=0.0,
+                 exchange_passes=0, ctas=0, max_restarts=0, timeout_s=0, time_kernels=False,
+                 stream=None):
+        self.lib = load()
+        self.code, self.dtype = _dtype_code(dtype)
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        n = len(self.shapes)
+        dims = np.ascontiguousarray([[sh[2], sh[1], sh[0]] for sh in self.shapes], dtype=np.int64)
+        hh = np.ascontiguousarray(hs, dtype=np.float64)
+        if hh.shape != (n,):
+            raise ValueError("one spacing per grid")
+        cfg = FmmConfig()
+        cfg.dtype = self.code
+        cfg.width = 0.0 if math.isinf(width) else float(width)
+        cfg.stride = float(stride)
+        cfg.bucket = float(bucket)
+        cfg.exchange_passes = int(exchange_passes)
+        cfg.ctas = int(ctas)
+        cfg.max_restarts = int(max_restarts)
+        cfg.timeout_s = int(timeout_s)
+        cfg.time_kernels = 1 if time_kernels else 0
+        cfg.stream = _stream_handle(stream)
+        handle = ctypes.c_void_p()
+        rc = self.lib.fmm_create_batch(n, dims.ctypes.data, hh.ctypes.data, ctypes.byref(cfg),
+                                       ctypes.byref(handle))
+        if rc != FMM_OK:
+            raise FmmError(rc, self.lib.fmm_last_error(None).decode())
+        self.handle = handle
+
+    def reinit(self, phis, T_outs=None, tags_outs=None, want_tags=True):
+        n = len(self.shapes)
+        if len(phis) != n:
+            raise ValueError("one level set per grid")
+        if T_outs is None:
+            T_outs = [torch.empty(sh, dtype=self.dtype, device="cuda") for sh in self.shapes]
+        if tags_outs is None and want_tags:
+            tags_outs = [torch.empty(sh, dtype=torch.uint8, device="cuda") for sh in self.shapes]
+        P = (ctypes.c_void_p * n)(*[_dev_ptr(p, self.dtype, sh, "phi0").value
+                                    for p, sh in zip(phis, self.shapes)])
+        To = (ctypes.c_void_p * n)(*[_dev_ptr(t, self.dtype, sh, "T_out").value
+                                     for t, sh in zip(T_outs, self.shapes)])
+        Go = None
+        if tags_outs is not None:
+            Go = (ctypes.c_void_p * n)(*[_dev_ptr(t, torch.uint8, sh, "tags_out").value
+                                         for t, sh in zip(tags_outs, self.shapes)])
+        rc = self.lib.fmm_reinit_batch(self.handle, P, To, Go)
+        if rc != FMM_OK:
+            raise FmmError(rc, self.lib.fmm_last_error(self.handle).decode())
+        return T_outs, tags_outs
+
+    def stats(self):
+        st = FmmStats()
+        rc = self.lib.fmm_get_stats(self.handle, ctypes.byref(st))
+        if rc != FMM_OK:
+            raise FmmError(rc, "fmm_get_stats failed")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=0.0, bucket=0.0,

@@ -275,6 +275,89 @@ def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream):
     return statistics.mean(times), nbytes, T_out.numel() * T_out.element_size()
 
 
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1):
+    """Heterogeneous speed F = exp(g/2) (16 random Fourier modes), 8 point
+    sources, L = sum of psi at 64 receiver cells: forward solve with the tape
+    and fmm_adjoint (dL/d slowness), each timed with CUDA events."""
+    p = wl.fourier_sources(n=n, n_sources=8, n_receivers=64, seed=3, device="cuda")
+    out = {"workload": f"fourier speed {n}^3, 8 sources, 64 receivers", "points": p.n_points}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        F = p.speed.to(dt).contiguous()
+        g = torch.zeros(p.shape, dtype=dt, device="cuda")
+        for i, j, k in p.receivers:
+            g[k, j, i] += 1.0
+        s = fmm.Solver(p.shape, p.h, dtype=dt, speed=F, sources=p.sources, record_tape=True,
+                       stream=stream)
+        T = torch.empty(p.shape, dtype=dt, device="cuda")
+        d = torch.empty(p.shape, dtype=dt, device="cuda")
+        fw, bw = [], []
+        for k in range(warmup + steps):
+            e0, e1 = _events(torch, stream)
+            e2, e3 = _events(torch, stream)
+            e0.record(stream)
+            s.solve(T, None, want_tags=False)
+            e1.record(stream)
+            e2.record(stream)
+            s.adjoint(g, d)
+            e3.record(stream)
+            e3.synchronize()
+            if k >= warmup:
+                fw.append(e0.elapsed_time(e1))
+                bw.append(e2.elapsed_time(e3))
+        st = s.stats()
+        s.close()
+        fms, bms = statistics.mean(fw), statistics.mean(bw)
+        out[name] = {"forward_gpts": p.n_points / fms / 1e6, "adjoint_gpts": p.n_points / bms / 1e6,
+                     "forward_ms": fms, "adjoint_ms": bms, "adjoint_vs_forward": fms / bms,
+                     "adjoint_iterations": st["adjoint_iterations"]}
+    return out
+
+
+def measure_batch(fmm, torch, wl, stream, steps=2, warmup=1):
+    """256 independent grids (each axis uniform in [32, 192]), 1-8 random
+    spheres each, fp32: one batched solve against the same grids solved one
+    after another with single-grid handles."""
+    probs = wl.batch(n_grids=256, lo=32, hi=192, seed=4, device="cuda")
+    phis = [p.phi0.to(torch.float32).contiguous() for p in probs]
+    pts = sum(p.n_points for p in probs)
+    b = fmm.Batch([p.shape for p in probs], [p.h for p in probs], dtype=torch.float32,
+                  stream=stream)
+    Ts = [torch.empty(p.shape, dtype=torch.float32, device="cuda") for p in probs]
+    tb = []
+    for k in range(warmup + steps):
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        b.reinit(phis, Ts, None, want_tags=False)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warmup:
+            tb.append(e0.elapsed_time(e1))
+    st = b.stats()
+    b.close()
+    solvers = [fmm.Solver(p.shape, p.h, dtype=torch.float32, stream=stream) for p in probs]
+    tp = []
+    for k in range(warmup + steps):
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        for s, ph, T in zip(solvers, phis, Ts):
+            s.reinit(ph, T, None, want_tags=False)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warmup:
+            tp.append(e0.elapsed_time(e1))
+    for s in solvers:
+        s.close()
+    bms, pms = statistics.mean(tb), statistics.mean(tp)
+    return {"workload": "256 grids, axes uniform in [32, 192], 1-8 spheres each, fp32",
+            "points": pts, "batched_gpts": pts / bms / 1e6, "batched_ms": bms,
+            "plain_gpts": pts / pms / 1e6, "plain_ms": pms, "batched_vs_plain": pms / bms,
+            "restarts": st["restarts"], "bricks": st["n_bricks"]}
+
+
 def run_gpu(args):
     ws, rank, local, pg = dist_setup()
     import torch
@@ -317,6 +400,9 @@ def run_gpu(args):
     e2e_ms = max_over_ranks(pg, e2e_ms)
     e2e_value = total_pts / (e2e_ms / 1e3) / 1e9
 
+    adjoint = measure_adjoint(fmm, torch, wl, stream)
+    batched = measure_batch(fmm, torch, wl, stream)
+
     if rank != 0:
         return 0
 
@@ -358,6 +444,8 @@ def run_gpu(args):
         "clocks": clocks,
         "fp64": {"value": total_pts / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
                  "roofline": roofline(r64, "f64")},
+        "adjoint": adjoint,
+        "batched": batched,
         "solve_stats": {k: st[k] for k in ("restarts", "brick_marches", "march_rounds",
                                             "exchanges", "accepted", "n_bricks")},
         "wall_ms_timed_region": wall_ms,

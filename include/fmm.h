@@ -75,9 +75,17 @@ typedef struct {
     void *stream;          /* cudaStream_t                                      */
     int32_t time_kernels;  /* 1: time every march launch with CUDA events on
                               the solve's stream (fmm_stats.march_ms)         */
-    int32_t exchange_passes; /* exchange + march passes after the first march
-                              of every restart (Algorithm 16 has 1); 0 -> the
-                              GB300 default (2 for FMM_F32, 1 for FMM_F64)   */
+    int32_t exchange_passes; /* phased schedule: exchange + march passes after
+                              the first march of every restart (Algorithm 16
+                              has 1); 0 -> 2 for FMM_F32, 1 for FMM_F64      */
+    int32_t schedule;      /* 0 -> persistent (the default); 1 phased: every
+                              restart is a select + march launch, then
+                              exchange_passes select + march launches, as in
+                              Algorithm 16; 2 persistent: one launch per
+                              restart marches every brick to the bound,
+                              re-queuing bricks whose halo changed until none
+                              is left                                         */
+    int32_t reserved2;
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */
@@ -96,6 +104,7 @@ typedef struct {
     int64_t adjoint_iterations; /* select + march passes of the last fmm_adjoint */
     int32_t error_flags;     /* device-side error bits (0 = none)                */
     int32_t reserved0;
+    int64_t cell_solves;     /* Algorithm 11 evaluations in the brick marches    */
 } fmm_stats;
 
 typedef struct fmm_handle fmm_handle;
@@ -183,6 +192,20 @@ fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const
 
 /* fmm_get_stats -- statistics of the last solve (synchronises the stream). */
 fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out);
+
+/* One march launch of the last solve (recorded when time_kernels is set). */
+typedef struct {
+    int32_t restart;   /* pass of the Algorithm 16 loop (1-based)          */
+    int32_t phase;     /* 0 = first march, 1.. = exchange passes           */
+    int32_t bricks;    /* bricks in the launch's work list                 */
+    float ms;          /* device time of the launch (CUDA events)          */
+} fmm_trace_entry;
+
+/* fmm_get_trace -- per-launch trace of the last solve on hd: copies up to
+ * capacity entries to out (host) and the number available to *n_out.
+ * Needs time_kernels = 1 in the handle's config (else *n_out = 0). */
+fmm_status fmm_get_trace(const fmm_handle *hd, fmm_trace_entry *out, int64_t capacity,
+                         int64_t *n_out);
 
 /* fmm_last_error -- message of the last failing call on hd, or of the last
  * failing fmm_create on this thread when hd is NULL.  Never NULL. */

@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
     AdjTile<real> &W = reinterpret_cast<AdjTile<real> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
     const long long n = (kMode == 0) ? g.nbricks : (long long)ctrl->n_list[which];
+    const int *work_list = which ? s.list[1] : s.list[0];
     const real *T = (const real *)s.T;
     const real *spd = (const real *)s.spd;
     const int off[3] = {1, kTile, kTile * kTile};
     for (long long it = (long long)blockIdx.x * kAdjWarps + warp; it < n;
          it += (long long)gridDim.x * kAdjWarps) {
-        const long long b = (kMode == 0) ? it : (long long)s.list[which][it];
+        const long long b = (kMode == 0) ? it : (long long)work_list[it];
         int bx, by, bz;
         brick_xyz(g, b, bx, by, bz);
         const long long base = b * kB3;

@@ -29,6 +29,9 @@ struct fmm_handle {
     long long pre_launches = 0;       // init launches of the current solve
     fmm_stats stats;
     std::vector<cudaEvent_t> events;   // march timing pairs (time_kernels)
+    int *d_trace = nullptr;            // 3 ints per march launch (time_kernels)
+    size_t trace_cap = 0;              // launches the trace buffer holds
+    std::vector<fmm_trace_entry> trace;
     void *adj_mu = nullptr;            // adjoint workspace (lambda / D per cell)
     unsigned *adj_count = nullptr;
     // batches (fmm_create_batch)
@@ -70,7 +73,7 @@ void free_state(fmm_handle *hd)
 {
     DeviceState &s = hd->st;
     void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.inbox, s.dirty,
-                    s.list[0], s.list[1], s.ctrl, hd->d_src};
+                    s.list[0], s.list[1], s.ctrl, hd->d_src, s.queue, s.queued};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -79,6 +82,10 @@ void free_state(fmm_handle *hd)
     for (cudaEvent_t e : hd->events)
         cudaEventDestroy(e);
     hd->events.clear();
+    if (hd->d_trace)
+        cudaFree(hd->d_trace);
+    hd->d_trace = nullptr;
+    hd->trace_cap = 0;
     if (hd->d_grids)
         cudaFree(hd->d_grids);
     if (hd->d_bgrid)
@@ -154,6 +161,8 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     FMM_CUDA(hd, launch_reset_control(s, st));
     FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     long long launches = 0;
     FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
     launches += 2;   // control reset, front init
@@ -167,9 +176,10 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     bool timed_out = false;
     long long batch = 1;
     for (;;) {
-        const size_t ev_per = 2 * (size_t)(1 + hd->params.passes);
+        const size_t ev_per = 2 * (size_t)marches_per_restart(hd->params.passes, hd->params.schedule);
         for (long long r = 0; r < batch; ++r) {
             cudaEvent_t *ev = nullptr;
+            int *tr = nullptr;
             if (timing) {
                 while (hd->events.size() < ev_used + ev_per) {
                     cudaEvent_t e;
@@ -177,10 +187,28 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
                     hd->events.push_back(e);
                 }
                 ev = &hd->events[ev_used];
+                const size_t launch_idx = ev_used / 2;
+                if (launch_idx + ev_per / 2 > hd->trace_cap) {
+                    // grow the trace buffer (between batches nothing is in
+                    // flight that writes to it)
+                    FMM_CUDA(hd, cudaStreamSynchronize(st));
+                    const size_t cap = 2 * (launch_idx + ev_per / 2) + 64;
+                    int *nb = nullptr;
+                    FMM_CUDA(hd, alloc(&nb, cap * 3 * sizeof(int)));
+                    if (hd->d_trace) {
+                        FMM_CUDA(hd, cudaMemcpy(nb, hd->d_trace, hd->trace_cap * 3 * sizeof(int),
+                                                cudaMemcpyDeviceToDevice));
+                        cudaFree(hd->d_trace);
+                    }
+                    hd->d_trace = nb;
+                    hd->trace_cap = cap;
+                }
+                tr = hd->d_trace + 3 * launch_idx;
                 ev_used += ev_per;
             }
-            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st, ev));
-            launches += launches_per_restart(hd->params.passes);
+            FMM_CUDA(hd, launch_restart(dt, g, s, hd->params, st, ev, tr));
+            launches += launches_per_restart(hd->params.passes, hd->params.schedule) +
+                        (timing ? marches_per_restart(hd->params.passes, hd->params.schedule) : 0);
         }
         FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
         FMM_CUDA(hd, cudaStreamSynchronize(st));
@@ -200,6 +228,7 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     hd->stats.march_rounds = (int64_t)c.rounds;
     hd->stats.exchanges = (int64_t)c.exchanges;
     hd->stats.accepted = (int64_t)c.accepted;
+    hd->stats.cell_solves = (int64_t)c.solves;
     hd->stats.n_bricks = g.nbricks;
     hd->stats.error_flags = c.error;
     if (T_out) {
@@ -209,7 +238,9 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     FMM_CUDA(hd, cudaStreamSynchronize(st));
     // restarts after the terminating pass only return; the march launches
     // that did work are those of every pass but the last
-    const long long worked = c.restart > 0 ? (1LL + hd->params.passes) * (c.restart - 1) : 0;
+    const long long worked =
+        c.restart > 0 ? (long long)marches_per_restart(hd->params.passes, hd->params.schedule) * (c.restart - 1)
+                      : 0;
     hd->stats.march_launches = worked;
     hd->stats.kernel_launches = launches + hd->pre_launches;
     hd->pre_launches = 0;
@@ -222,12 +253,29 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
         }
     }
     hd->stats.march_ms = ms;
+    hd->trace.clear();
+    if (timing && worked > 0) {
+        std::vector<int> tr((size_t)worked * 3);
+        FMM_CUDA(hd, cudaMemcpy(tr.data(), hd->d_trace, tr.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < worked; ++k) {
+            fmm_trace_entry e;
+            e.restart = tr[3 * k];
+            e.phase = tr[3 * k + 1];
+            e.bricks = tr[3 * k + 2];
+            float t = 0.f;
+            FMM_CUDA(hd, cudaEventElapsedTime(&t, hd->events[2 * k], hd->events[2 * k + 1]));
+            e.ms = t;
+            hd->trace.push_back(e);
+        }
+    }
     hd->solved = true;
     hd->tape_valid = s.tape != nullptr;
     if (timed_out)
         return fail(hd, FMM_ERR_TIMEOUT, "the solve exceeded its wall-clock limit (timeout_s)");
     if (c.error & ERR_ROUNDS)
         return fail(hd, FMM_ERR_TIMEOUT, "a brick march exceeded its round limit");
+    if (c.error & ERR_SPIN)
+        return fail(hd, FMM_ERR_TIMEOUT, "a bounded wait of the persistent march gave up");
     if (c.error & ERR_RESTARTS)
         return fail(hd, FMM_ERR_TIMEOUT, "the restart limit was reached before termination");
     return FMM_OK;
@@ -265,6 +313,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return fail(nullptr, FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
     if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
         return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
+    if (cfg->schedule < 0 || cfg->schedule > 2)
+        return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1 or 2");
     if (n_src < 0 || (n_src > 0 && !src_ijk))
         return fail(nullptr, FMM_ERR_INVALID, "bad source list");
     if (speed && !aligned16(speed))
@@ -299,6 +349,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     p.stride = stride_h * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
+    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
 
@@ -331,6 +382,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     ALLOC(s.dirty, nb * sizeof(unsigned));
     ALLOC(s.list[0], nb * sizeof(int));
     ALLOC(s.list[1], nb * sizeof(int));
+    ALLOC(s.queue, nb * sizeof(unsigned long long));
+    ALLOC(s.queued, nb * sizeof(unsigned));
     ALLOC(s.ctrl, sizeof(Control));
     if (cfg->record_tape)
         ALLOC(s.tape, cells);
@@ -534,6 +587,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * hmin;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
+    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.spd_term = 0.0;
@@ -567,6 +621,8 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     ALLOC(s.dirty, nb * sizeof(unsigned));
     ALLOC(s.list[0], nb * sizeof(int));
     ALLOC(s.list[1], nb * sizeof(int));
+    ALLOC(s.queue, nb * sizeof(unsigned long long));
+    ALLOC(s.queued, nb * sizeof(unsigned));
     ALLOC(s.ctrl, sizeof(Control));
     ALLOC(hd->d_nbr, nb * kFaces * sizeof(int));
     ALLOC(hd->d_bgrid, nb * sizeof(int));
@@ -625,6 +681,18 @@ fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const
     FMM_CUDA(hd, launch_batch_output(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
     FMM_CUDA(hd, cudaStreamSynchronize(st));
     hd->stats.kernel_launches += 1;
+    return FMM_OK;
+}
+
+fmm_status fmm_get_trace(const fmm_handle *hd, fmm_trace_entry *out, int64_t capacity,
+                         int64_t *n_out)
+{
+    if (!hd || !n_out || capacity < 0 || (capacity > 0 && !out))
+        return FMM_ERR_INVALID;
+    *n_out = (int64_t)hd->trace.size();
+    const size_t n = hd->trace.size() < (size_t)capacity ? hd->trace.size() : (size_t)capacity;
+    for (size_t i = 0; i < n; ++i)
+        out[i] = hd->trace[i];
     return FMM_OK;
 }
 

@@ -37,6 +37,7 @@ enum : int {
     ERR_ROUNDS = 1,       // a brick march exceeded its round limit
     ERR_RESTARTS = 2,     // the restart limit was reached
     ERR_SPEED = 4,        // a speed value was not finite and > 0
+    ERR_SPIN = 8,         // a bounded wait of the persistent march gave up
 };
 
 // Restart control block of Algorithm 16, in device memory.
@@ -47,6 +48,7 @@ struct Control {
     unsigned long long rounds;
     unsigned long long exchanges;
     unsigned long long accepted;
+    unsigned long long solves;       // Algorithm 11 evaluations
     double bound[2];                 // bound_band(-1), bound_band(+1)
     unsigned int dirty_count;        // count_global: bricks with pending
                                      // overlap changes
@@ -56,6 +58,13 @@ struct Control {
     int error;
     int restart;
     int pad;
+    // persistent march: ring queue positions and the count of bricks pushed
+    // and not yet marched, each on a line of its own (they are the only
+    // words every warp touches)
+    alignas(128) unsigned long long q_head;
+    alignas(128) unsigned long long q_tail;
+    alignas(128) int pending;
+    int pad2[31];
 };
 
 struct Geom {
@@ -75,7 +84,11 @@ struct SolveParams {
     long long max_restarts;
     int max_rounds;     // per brick march
     int passes;         // exchange + march passes after the first march
+    int schedule;       // kSchedulePhased or kSchedulePersistent
 };
+
+constexpr int kSchedulePhased = 1;
+constexpr int kSchedulePersistent = 2;
 
 // Defaults of the restart parameters (units of h and of the bucket width),
 // measured on GB300 for 8^3 bricks.
@@ -96,6 +109,8 @@ struct DeviceState {
     unsigned int *dirty;         // 1 per brick: has pending overlap changes
     int *list[2];       // work lists
     const int *nbr;     // 6 per brick: neighbour brick or -1 (batches only)
+    unsigned long long *queue;   // persistent march: ring of (seq << 32 | brick + 1)
+    unsigned *queued;            // per brick: in the queue or being marched
     Control *ctrl;
     int march_ctas;
 };
@@ -128,9 +143,18 @@ cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
 // march, then p.passes exchange passes (select + march, with a list reset
 // before every pass but the first).  ev, when not null, holds one event pair
 // per march launch (2 * (1 + passes) events).
-inline int launches_per_restart(int passes) { return 2 + 2 * (1 + passes) + (passes - 1); }
+inline int launches_per_restart(int passes, int schedule)
+{
+    return schedule == kSchedulePersistent ? 4 : 2 + 2 * (1 + passes) + (passes - 1);
+}
+// march launches (timed, traced) per restart
+inline int marches_per_restart(int passes, int schedule)
+{
+    return schedule == kSchedulePersistent ? 1 : 1 + passes;
+}
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
-                           const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev);
+                           const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev,
+                           int *trace);
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);

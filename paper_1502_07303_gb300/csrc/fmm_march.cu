@@ -389,10 +389,12 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
 // accepted).  kMode 1: Algorithm 12 up to the restart bound over the bricks
 // of work list `which`.
 //
-// Cell sets of a brick are 512-bit masks held as sixteen 32-bit words; lane k
-// (k < 16) holds word k, which covers the cells 32k .. 32k+31, i.e. z = k/2,
-// y = 4(k%2) .. 4(k%2)+3, all x (bit = x + 8 (y % 4)).  The cells to solve in
-// a round are compacted into a list so that all 32 lanes do useful work.
+// Lane l owns the 16 cells c = l + 32 k (k = 0..15) of the brick: x = l % 8,
+// y = (l / 8) % 4 + 4 (k % 2), z = k / 2.  Cell sets (BAND, KNOWN, frozen,
+// side, accepted, to-solve) are 16-bit masks per lane, bit k for cell
+// l + 32 k, so the per-round passes touch only the cells in a set.  The cells
+// to solve in a round are compacted into a list by a warp prefix sum, so all
+// 32 lanes solve.
 // ---------------------------------------------------------------------------
 
 constexpr int kMarchWarps = 4;   // bricks in flight per CTA
@@ -400,11 +402,11 @@ constexpr unsigned FULL = 0xffffffffu;
 
 template <typename real>
 struct WarpTile {
-    real kv[kTile3];      // known values of the brick and its face halo
-    real tv[kB3];         // current |psi| of the brick's cells
-    uint8_t tg[kB3];      // tags
-    uint8_t tp[kB3];      // upwind sets (tape)
-    uint16_t list[kB3];   // compacted cells to solve
+    real kv[kTile3];       // known values of the brick and its face halo
+    real tv[kB3];          // current |psi| of the brick's cells
+    uint8_t tp[kB3];       // upwind sets (tape)
+    uint16_t list[kB3];    // compacted cells to solve
+    unsigned improved[32]; // per owner lane: cells whose value dropped
 };
 
 __device__ __forceinline__ int tile_of(int c)
@@ -412,119 +414,130 @@ __device__ __forceinline__ int tile_of(int c)
     return 111 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
 }
 
-// Cells of word k (lane k) next to a cell of the 512-bit set A (same layout).
-__device__ __forceinline__ unsigned neighbour_words(unsigned A, int lane)
+// Cells of lane l next to a cell of the set A (16-bit lane masks).
+__device__ __forceinline__ unsigned neighbour_mask(unsigned A, int lane)
 {
-    const unsigned Ap1 = __shfl_down_sync(FULL, A, 1);
-    const unsigned Am1 = __shfl_up_sync(FULL, A, 1);
-    const unsigned Ap2 = __shfl_down_sync(FULL, A, 2);
-    const unsigned Am2 = __shfl_up_sync(FULL, A, 2);
-    unsigned r = ((A << 1) & 0xFEFEFEFEu) | ((A >> 1) & 0x7F7F7F7Fu);   // x -/+ 1
-    r |= (A << 8) | (A >> 8);                                            // y inside the word
-    if (lane & 1)
-        r |= Am1 >> 24;                                                  // y = 3 -> y = 4
-    else
-        r |= Ap1 << 24;                                                  // y = 4 -> y = 3
-    if (lane >= 2)
-        r |= Am2;                                                        // z - 1
-    if (lane + 2 < 16)
-        r |= Ap2;                                                        // z + 1
-    return lane < 16 ? r : 0u;
+    const int x = lane & 7, r = (lane >> 3) & 3;
+    const unsigned axm = __shfl_up_sync(FULL, A, 1);
+    const unsigned axp = __shfl_down_sync(FULL, A, 1);
+    const unsigned aym = __shfl_up_sync(FULL, A, 8);
+    const unsigned ayp = __shfl_down_sync(FULL, A, 8);
+    const unsigned ay3 = __shfl_down_sync(FULL, A, 24);   // lanes 0..7 read row 3
+    const unsigned ay0 = __shfl_up_sync(FULL, A, 24);     // lanes 24..31 read row 0
+    unsigned n = (A << 2) | (A >> 2);                     // z -/+ 1
+    if (x > 0)
+        n |= axm;
+    if (x < 7)
+        n |= axp;
+    if (r > 0)
+        n |= aym;
+    if (r < 3)
+        n |= ayp;
+    if (r == 0)
+        n |= (ay3 << 1) & 0xAAAAu;     // y = 3 (slot k-1) -> y = 4 (odd slot k)
+    if (r == 3)
+        n |= (ay0 >> 1) & 0x5555u;     // y = 4 (slot k+1) -> y = 3 (even slot k)
+    return n & 0xFFFFu;
 }
 
-// Cells of word k next to a halo cell flagged in the per-face masks F[6]
+// Cells of lane l next to a halo cell flagged in the per-face masks F[6]
 // (face bit = u + 8 v with (u, v) the two in-face coordinates).
-__device__ __forceinline__ unsigned face_words(const unsigned long long F[kFaces], int k)
+__device__ __forceinline__ unsigned face_mask(const unsigned long long F[kFaces], int lane)
 {
-    if (k >= 16)
-        return 0u;
-    const int z = k >> 1, y0 = 4 * (k & 1);
-    unsigned r = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int bit = y0 + j + 8 * z;
-        if ((F[0] >> bit) & 1ull)
-            r |= 1u << (8 * j);
-        if ((F[1] >> bit) & 1ull)
-            r |= 1u << (8 * j + 7);
+    const int x = lane & 7, r = (lane >> 3) & 3;
+    unsigned n = 0;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int y = r + 4 * (k & 1), z = k >> 1;
+        bool hit = false;
+        if (x == 0)
+            hit = hit || ((F[0] >> (y + 8 * z)) & 1ull);
+        if (x == 7)
+            hit = hit || ((F[1] >> (y + 8 * z)) & 1ull);
+        if (y == 0)
+            hit = hit || ((F[2] >> (x + 8 * z)) & 1ull);
+        if (y == 7)
+            hit = hit || ((F[3] >> (x + 8 * z)) & 1ull);
+        if (z == 0)
+            hit = hit || ((F[4] >> (x + 8 * y)) & 1ull);
+        if (z == 7)
+            hit = hit || ((F[5] >> (x + 8 * y)) & 1ull);
+        if (hit)
+            n |= 1u << k;
     }
-    if ((k & 1) == 0)
-        r |= (unsigned)((F[2] >> (8 * z)) & 0xFFull);
-    else
-        r |= (unsigned)((F[3] >> (8 * z)) & 0xFFull) << 24;
-    if (k < 2)
-        r |= (unsigned)(F[4] >> (32 * (k & 1)));
-    if (k >= 14)
-        r |= (unsigned)(F[5] >> (32 * (k & 1)));
-    return r;
+    return n;
 }
 
-template <typename real, bool kHetero, int kMode>
-__global__ void __launch_bounds__(kMarchWarps * 32)
-    k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
+struct MarchStats {
+    unsigned long long marches, rounds, accepted, exchanges, solves;
+};
+
+// One brick march.  F_in: the halo cells whose known value changed since the
+// brick last ran (kMode 1); kMode 0 derives them from the known halo cells.
+// kFresh: read the brick and halo through L2 (the persistent kernel, where the
+// brick may have been written by another SM during the same launch).  On
+// return, lanes 0..5 hold in notify_m / notify_nb the changed boundary cells
+// and the neighbour brick across face = lane (mode 1).
+template <typename real, bool kHetero, int kMode, bool kFresh>
+__device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s, const SolveParams &p,
+                                            double spd_const_term, WarpTile<real> &W, long long b,
+                                            const unsigned long long *F_in, real bound0, real bound1,
+                                            int lane, unsigned long long &notify_m,
+                                            long long &notify_nb, MarchStats &st)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
-    Control *ctrl = s.ctrl;
-    if (kMode == 1 && ctrl->done)
-        return;
-    const long long n = (kMode == 0) ? g.nbricks : (long long)ctrl->n_list[which];
     real *T = (real *)s.T;
     uint8_t *tag = s.tag;
     const real *spd = (const real *)s.spd;
     const real *bdelta = (const real *)s.bdelta;
     real *bmin = (real *)s.bmin;
     const real INF = inf_v<real>();
-    const real bound0 = (real)ctrl->bound[0], bound1 = (real)ctrl->bound[1];
-    const unsigned lanemask_lt = (1u << lane) - 1u;
-    unsigned long long st_marches = 0, st_rounds = 0, st_acc = 0, st_exch = 0;
-
-    // bricks of the work list are taken one at a time from a shared counter
-    // (the next index is fetched while the current brick is processed)
-    long long it = 0, next = 0;
-    if (kMode == 1) {
-        if (lane == 0) {
-            it = (long long)atomicAdd(&ctrl->work[which], 1u);
-            next = (long long)atomicAdd(&ctrl->work[which], 1u);
-        }
-        it = __shfl_sync(FULL, it, 0);
-        next = __shfl_sync(FULL, next, 0);
-    } else {
-        it = (long long)blockIdx.x * kMarchWarps + warp;
-    }
-    while (it < n) {
-        const long long b = (kMode == 0) ? it : (long long)s.list[which][it];
-        long long nbi[kFaces];
+    const int lx = lane & 7, lr = (lane >> 3) & 3;
+    long long nbi[kFaces];
 #pragma unroll
-        for (int f = 0; f < kFaces; ++f)
-            nbi[f] = neighbour_brick(g, s.nbr, b, f);
-        const long long base = b * kB3;
+    for (int f = 0; f < kFaces; ++f)
+        nbi[f] = neighbour_brick(g, s.nbr, b, f);
+    const long long base = b * kB3;
 
-        // ---- stage the brick (owned by this warp: plain loads) ------------
+    // ---- stage the brick ---------------------------------------------------
+    unsigned band = 0, known = 0, fix = 0, out = 0, neg = 0;
+    real r0 = INF, r1 = INF;   // lane minimum of the BAND cells of each side
 #pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            const int c = lane + 32 * k;
-            const real v = T[base + c];
-            const uint8_t t = tag[base + c];
-            W.tv[c] = v;
-            W.tg[c] = t;
-            W.kv[tile_of(c)] = is_known(t) ? v : INF;
-            if (s.tape)
-                W.tp[c] = s.tape[base + c];
+    for (int k = 0; k < 16; ++k) {
+        const int c = lane + 32 * k;
+        const real v = kFresh ? __ldcg(T + base + c) : T[base + c];
+        const uint8_t t = kFresh ? __ldcg(tag + base + c) : tag[base + c];
+        const uint8_t sv = t & ST_MASK;
+        W.tv[c] = v;
+        W.kv[tile_of(c)] = sv >= ST_KNOWN ? v : INF;
+        if (s.tape)
+            W.tp[c] = kFresh ? __ldcg(s.tape + base + c) : s.tape[base + c];
+        band |= (unsigned)(sv == ST_BAND) << k;
+        known |= (unsigned)(sv >= ST_KNOWN) << k;
+        fix |= (unsigned)(sv == ST_FIX) << k;
+        out |= (unsigned)((t & TG_OUT) != 0) << k;
+        neg |= (unsigned)((t & TG_NEG) != 0) << k;
+        if (sv == ST_BAND) {
+            if (t & TG_NEG)
+                r0 = vmin(r0, v);
+            else
+                r1 = vmin(r1, v);
         }
-        // ---- halo: the face layers of the six neighbours (read-only) ------
-        unsigned long long F[kFaces];
+    }
+    W.improved[lane] = 0u;
+    const unsigned frozen = fix | out;
+    // ---- halo: the face layers of the six neighbours (read-only) ----------
+    unsigned long long F[kFaces];
 #pragma unroll
-        for (int f = 0; f < kFaces; ++f)
-            F[f] = 0ull;
+    for (int f = 0; f < kFaces; ++f)
+        F[f] = kMode == 0 ? 0ull : F_in[f];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int h = lane + 32 * k;
-            const int f = h >> 6, q = h & 63, u = q & 7, v = q >> 3;
-            const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
+    for (int f = 0; f < kFaces; ++f) {
+        const long long nb = nbi[f];
+        const int axis = f >> 1, dir = (f & 1) ? 1 : -1;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int q = lane + 32 * half, u = q & 7, v = q >> 3;
             real val = INF;
-            const long long nb = nbi[k >> 1];
             if (nb >= 0) {
                 const int edge = dir < 0 ? kB - 1 : 0;
                 const int cx = axis == 0 ? edge : u;
@@ -544,208 +557,483 @@ __global__ void __launch_bounds__(kMarchWarps * 32)
             if (kMode == 0) {
                 // Algorithm 9: every known halo cell updates its neighbours
                 const unsigned bal = __ballot_sync(FULL, lt(val, INF));
-                F[k >> 1] |= (unsigned long long)bal << (32 * (k & 1));
+                F[f] |= (unsigned long long)bal << (32 * half);
             }
         }
-        if (kMode == 1) {
-            // changed halo cells, snapshotted by the select kernel
-#pragma unroll
-            for (int f = 0; f < kFaces; ++f)
-                F[f] = s.inbox[b * kFaces + f];
-        }
-        __syncwarp();
+    }
+    __syncwarp();
 
-        // ---- masks: frozen (FIX or padding) and known cells ----------------
-        unsigned frozen_w = 0, known_w = 0;
+    unsigned relax = face_mask(F, lane);
+    if (kMode == 0)
+        relax |= neighbour_mask(known, lane);
+    relax &= ~frozen;
+
+    const real delta = (real)p.bucket * bdelta[b];
+    unsigned acc_any = 0;
+    int rounds = 0;
+    real m0 = INF, m1 = INF;
+    // Settled cells: KNOWN cells at or below the band minimum of their side.
+    // No later acceptance in this march can lower them: the band minimum
+    // never falls within a march (a value computed from an accepted
+    // neighbour v is a causal root, so it exceeds v, and v is at least the
+    // minimum), every accepted value is at least that minimum, and an update
+    // from an upwind value v never goes below v.  They are left out of the
+    // solves.  pend: cells accepted at or below lim (pl0, pl1) that settle once
+    // the minimum of their side reaches it.
+    unsigned settled = 0, pend = 0;
+    real pl0 = INF, pl1 = INF;
+    for (;;) {
+        // compact the cells to solve (warp prefix sum of the lane counts)
+        const int cnt = __popc(relax);
+        int pre = cnt;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const uint8_t t = W.tg[lane + 32 * k];
-            const unsigned fz = __ballot_sync(FULL, ((t & ST_MASK) == ST_FIX) || (t & TG_OUT));
-            const unsigned kn = __ballot_sync(FULL, is_known(t));
-            if (lane == k) {
-                frozen_w = fz;
-                known_w = kn;
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, pre, o);
+            if (lane >= o)
+                pre += t;
         }
-        unsigned relax_w = face_words(F, lane);
+        const int n_items = __shfl_sync(FULL, pre, 31);
+        pre -= cnt;
+        st.solves += (unsigned long long)n_items;
+        for (unsigned m = relax; m; m &= m - 1u)
+            W.list[pre++] = (uint16_t)(lane + 32 * (__ffs(m) - 1));
+        __syncwarp();
+        // Algorithm 10/11: solve, then apply (Jacobi within 32 cells)
+        for (int i0 = 0; i0 < n_items; i0 += 32) {
+            const int i = i0 + lane;
+            int c = -1;
+            real cand = INF;
+            uint8_t cset = 0;
+            if (i < n_items) {
+                c = W.list[i];
+                const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
+                cand = solve_cell<real>(W.kv, tile_of(c), W.tv[c], sp, cset);
+            }
+            __syncwarp();
+            if (c >= 0 && lt(cand, W.tv[c])) {
+                W.tv[c] = cand;
+                W.kv[tile_of(c)] = INF;
+                W.tp[c] = cset;
+                atomicOr(&W.improved[c & 31], 1u << (c >> 5));
+            }
+            __syncwarp();
+        }
+        // a cell whose value dropped is BAND again (Algorithm 10)
+        const unsigned imp = W.improved[lane];
+        W.improved[lane] = 0u;
+        band |= imp;
+        known &= ~imp;
+        settled &= ~imp;
+        pend &= ~imp;
+        // minimum of the BAND cells of each side (the heap tops): the cells
+        // the last accept scan left plus the cells that just dropped
+        real l0 = r0, l1 = r1;
+        for (unsigned m = imp; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            const real v = W.tv[lane + 32 * k];
+            if ((neg >> k) & 1u)
+                l0 = vmin(l0, v);
+            else
+                l1 = vmin(l1, v);
+        }
+        m0 = warp_min(l0);
+        m1 = warp_min(l1);
         if (kMode == 0)
-            relax_w |= neighbour_words(known_w, lane);
-        relax_w &= ~frozen_w;
-
-        const real delta = (real)p.bucket * bdelta[b];
-        unsigned acc_any_w = 0;
-        int rounds = 0;
-        real m0 = INF, m1 = INF;
-        for (;;) {
-            // compact the cells to solve
-            int n_items = 0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const unsigned word = __shfl_sync(FULL, relax_w, k);
-                if ((word >> lane) & 1u)
-                    W.list[n_items + __popc(word & lanemask_lt)] = (uint16_t)(32 * k + lane);
-                n_items += __popc(word);
+            break;
+        if (rounds == 0) {
+            // cells that were KNOWN when the march began
+            for (unsigned m = known & ~settled; m; m &= m - 1u) {
+                const int k = __ffs(m) - 1;
+                if (!lt((neg >> k) & 1u ? m0 : m1, W.tv[lane + 32 * k]))
+                    settled |= 1u << k;
             }
-            __syncwarp();
-            // Algorithm 10/11: solve, then apply (Jacobi within 32 cells)
-            for (int i0 = 0; i0 < n_items; i0 += 32) {
-                const int i = i0 + lane;
-                int c = -1;
-                real cand = INF;
-                uint8_t cset = 0;
-                if (i < n_items) {
-                    c = W.list[i];
-                    const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
-                    cand = solve_cell<real>(W.kv, tile_of(c), W.tv[c], sp, cset);
-                }
-                __syncwarp();
-                if (c >= 0 && lt(cand, W.tv[c])) {
-                    W.tv[c] = cand;
-                    W.tg[c] = (uint8_t)((W.tg[c] & ~ST_MASK) | ST_BAND);
-                    W.kv[tile_of(c)] = INF;
-                    W.tp[c] = cset;
-                }
-                __syncwarp();
-            }
-            // minimum of the BAND cells of each side (the heap tops)
-            real l0 = INF, l1 = INF;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int c = lane + 32 * k;
-                const uint8_t t = W.tg[c];
-                if ((t & ST_MASK) == ST_BAND) {
-                    const real v = W.tv[c];
-                    if (t & TG_NEG)
-                        l0 = vmin(l0, v);
-                    else
-                        l1 = vmin(l1, v);
-                }
-            }
-            m0 = warp_min(l0);
-            m1 = warp_min(l1);
-            if (kMode == 0)
-                break;
-            // accept the lowest bucket up to the restart bound
-            const real lim0 = vmin(m0 + delta, bound0), lim1 = vmin(m1 + delta, bound1);
-            unsigned acc_w = 0;
-            int nacc = 0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int c = lane + 32 * k;
-                const uint8_t t = W.tg[c];
-                bool a = false;
-                if ((t & ST_MASK) == ST_BAND) {
-                    const real v = W.tv[c];
-                    a = !lt((t & TG_NEG) ? lim0 : lim1, v);
-                    if (a) {
-                        W.tg[c] = (uint8_t)((t & ~ST_MASK) | ST_KNOWN);
-                        W.kv[tile_of(c)] = v;
-                    }
-                }
-                const unsigned bw = __ballot_sync(FULL, a);
-                if (lane == k)
-                    acc_w = bw;
-                nacc += __popc(bw);
-            }
-            if (nacc == 0)
-                break;
-            acc_any_w |= acc_w;
-            st_acc += (unsigned long long)nacc;
-            if (++rounds > p.max_rounds) {
-                if (lane == 0)
-                    atomicOr(&ctrl->error, ERR_ROUNDS);
-                break;
-            }
-            __syncwarp();
-            relax_w = neighbour_words(acc_w, lane) & ~frozen_w;
         }
-
-        // ---- write back, front minima, overlap change notification --------
-        // A boundary cell accepted here (and known at the end) is flagged to
-        // the neighbour only if the adjacent halo cell is not known with a
-        // value at or below it: such a neighbour cell can never take it as an
-        // upwind value (Algorithm 11 uses only smaller known neighbours, and
-        // values only decrease), so the exchange would change nothing there.
-        unsigned long long fo0 = 0, fo1 = 0, fo2 = 0, fo3 = 0, fo4 = 0, fo5 = 0;
-        const int x = lane & 7, yl = (lane >> 3) & 3;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        if (!lt(m0, pl0)) {
+            settled |= pend & neg;
+            pend &= ~neg;
+        }
+        if (!lt(m1, pl1)) {
+            settled |= pend & ~neg;
+            pend &= neg;
+        }
+        // accept the lowest bucket up to the restart bound; the rest give
+        // the band minimum of the next round
+        const real lim0 = vmin(m0 + delta, bound0), lim1 = vmin(m1 + delta, bound1);
+        unsigned acc = 0;
+        r0 = INF;
+        r1 = INF;
+        for (unsigned m = band; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
             const int c = lane + 32 * k;
-            const uint8_t t = W.tg[c];
             const real v = W.tv[c];
-            T[base + c] = v;
-            tag[base + c] = t;
-            if (s.tape)
-                s.tape[base + c] = W.tp[c];
-            if (kMode == 1) {
-                const unsigned acc_word = __shfl_sync(FULL, acc_any_w, k);
-                if (((acc_word >> lane) & 1u) && is_known(t)) {
-                    const int y = yl + 4 * (k & 1), z = k >> 1;
-                    const int ti = tile_of(c);
-                    if (x == 0 && lt(v, W.kv[ti - 1]))
-                        fo0 |= 1ull << (y + 8 * z);
-                    if (x == 7 && lt(v, W.kv[ti + 1]))
-                        fo1 |= 1ull << (y + 8 * z);
-                    if (y == 0 && lt(v, W.kv[ti - kTile]))
-                        fo2 |= 1ull << (x + 8 * z);
-                    if (y == 7 && lt(v, W.kv[ti + kTile]))
-                        fo3 |= 1ull << (x + 8 * z);
-                    if (z == 0 && lt(v, W.kv[ti - kTile * kTile]))
-                        fo4 |= 1ull << (x + 8 * y);
-                    if (z == 7 && lt(v, W.kv[ti + kTile * kTile]))
-                        fo5 |= 1ull << (x + 8 * y);
-                }
+            const bool ng = (neg >> k) & 1u;
+            if (!lt(ng ? lim0 : lim1, v)) {
+                acc |= 1u << k;
+                W.kv[tile_of(c)] = v;
+            } else if (ng) {
+                r0 = vmin(r0, v);
+            } else {
+                r1 = vmin(r1, v);
             }
         }
-        if (lane == 0) {
-            bmin[2 * b] = m0;
-            bmin[2 * b + 1] = m1;
-        }
-        if (kMode == 1) {
-            unsigned long long out[kFaces] = {fo0, fo1, fo2, fo3, fo4, fo5};
-            unsigned long long m = 0;
-#pragma unroll
-            for (int f = 0; f < kFaces; ++f) {
-                const unsigned lo = __reduce_or_sync(FULL, (unsigned)out[f]);
-                const unsigned hi = __reduce_or_sync(FULL, (unsigned)(out[f] >> 32));
-                if (lane == f)
-                    m = (unsigned long long)lo | ((unsigned long long)hi << 32);
-            }
-            long long nbl = -1;
-#pragma unroll
-            for (int f = 0; f < kFaces; ++f)
-                if (lane == f)
-                    nbl = nbi[f];
-            if (lane < kFaces && m) {
-                const int f = lane;
-                if (nbl >= 0) {
-                    const long long nb = nbl;
-                    atomicOr(&s.fresh[nb * kFaces + (f ^ 1)], m);
-                    s.dirty[nb] = 1u;
-                    st_exch += (unsigned long long)__popcll(m);
-                }
-            }
-            st_marches += 1;
-            st_rounds += (unsigned long long)rounds;
+        band &= ~acc;
+        known |= acc;
+        const int nacc = __reduce_add_sync(FULL, (unsigned)__popc(acc));
+        if (nacc == 0)
+            break;
+        acc_any |= acc;
+        pend |= acc;
+        pl0 = lim0;
+        pl1 = lim1;
+        st.accepted += (unsigned long long)nacc;
+        if (++rounds > p.max_rounds) {
+            if (lane == 0)
+                atomicOr(&s.ctrl->error, ERR_ROUNDS);
+            break;
         }
         __syncwarp();
-        // next brick (dynamic scheduling)
+        relax = neighbour_mask(acc, lane) & ~frozen & ~settled;
+    }
+
+    // ---- write back, front minima, overlap change notification ------------
+    // A boundary cell accepted here (and known at the end) is flagged to the
+    // neighbour only if the adjacent halo cell is not known with a value at or
+    // below it: such a neighbour cell can never take it as an upwind value
+    // (Algorithm 11 uses only smaller known neighbours, and values only
+    // decrease), so the exchange would change nothing there.
+    unsigned long long fo0 = 0, fo1 = 0, fo2 = 0, fo3 = 0, fo4 = 0, fo5 = 0;
+    const unsigned chg = acc_any & known;
+#pragma unroll 2
+    for (int k = 0; k < 16; ++k) {
+        const int c = lane + 32 * k;
+        const real v = W.tv[c];
+        uint8_t t;
+        if ((out >> k) & 1u)
+            t = TG_OUT | ST_FAR;
+        else if ((fix >> k) & 1u)
+            t = ST_FIX;
+        else if ((known >> k) & 1u)
+            t = ST_KNOWN;
+        else if ((band >> k) & 1u)
+            t = ST_BAND;
+        else
+            t = ST_FAR;
+        if ((neg >> k) & 1u)
+            t |= TG_NEG;
+        T[base + c] = v;
+        tag[base + c] = t;
+        if (s.tape)
+            s.tape[base + c] = W.tp[c];
+        if (kMode == 1 && ((chg >> k) & 1u)) {
+            const int y = lr + 4 * (k & 1), z = k >> 1;
+            const int ti = tile_of(c);
+            if (lx == 0 && lt(v, W.kv[ti - 1]))
+                fo0 |= 1ull << (y + 8 * z);
+            if (lx == 7 && lt(v, W.kv[ti + 1]))
+                fo1 |= 1ull << (y + 8 * z);
+            if (y == 0 && lt(v, W.kv[ti - kTile]))
+                fo2 |= 1ull << (lx + 8 * z);
+            if (y == 7 && lt(v, W.kv[ti + kTile]))
+                fo3 |= 1ull << (lx + 8 * z);
+            if (z == 0 && lt(v, W.kv[ti - kTile * kTile]))
+                fo4 |= 1ull << (lx + 8 * y);
+            if (z == 7 && lt(v, W.kv[ti + kTile * kTile]))
+                fo5 |= 1ull << (lx + 8 * y);
+        }
+    }
+    if (lane == 0) {
+        bmin[2 * b] = m0;
+        bmin[2 * b + 1] = m1;
+    }
+    notify_m = 0;
+    notify_nb = -1;
+    if (kMode == 1) {
+        unsigned long long m = 0;
+#define FMM_FACE_OR(f, val)                                                        \
+    {                                                                              \
+        const unsigned lo = __reduce_or_sync(FULL, (unsigned)(val));               \
+        const unsigned hi = __reduce_or_sync(FULL, (unsigned)((val) >> 32));       \
+        if (lane == (f))                                                           \
+            m = (unsigned long long)lo | ((unsigned long long)hi << 32);           \
+    }
+        FMM_FACE_OR(0, fo0) FMM_FACE_OR(1, fo1) FMM_FACE_OR(2, fo2)
+        FMM_FACE_OR(3, fo3) FMM_FACE_OR(4, fo4) FMM_FACE_OR(5, fo5)
+#undef FMM_FACE_OR
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            if (lane == f)
+                notify_nb = nbi[f];
+        notify_m = (lane < kFaces && notify_nb >= 0) ? m : 0ull;
+        st.marches += 1;
+        st.rounds += (unsigned long long)rounds;
+    }
+}
+
+__device__ __forceinline__ void flush_stats(Control *ctrl, MarchStats &st, int lane)
+{
+    const unsigned ex = __reduce_add_sync(FULL, (unsigned)st.exchanges);
+    if (lane == 0 && st.marches) {
+        atomicAdd(&ctrl->marches, st.marches);
+        atomicAdd(&ctrl->rounds, st.rounds);
+        atomicAdd(&ctrl->accepted, st.accepted);
+        atomicAdd(&ctrl->solves, st.solves);
+        atomicAdd(&ctrl->exchanges, (unsigned long long)ex);
+    }
+}
+
+// Phased march: kMode 0 runs Algorithm 9 over all bricks; kMode 1 runs
+// Algorithm 12 over the bricks of work list `which` (taken one at a time from
+// a shared counter) with the change masks the select kernel moved to the
+// inbox; changes are flagged in the neighbours' live masks and dirty flags.
+template <typename real, bool kHetero, int kMode>
+__global__ void __launch_bounds__(kMarchWarps * 32, 4)
+    k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    Control *ctrl = s.ctrl;
+    if (kMode == 1 && ctrl->done)
+        return;
+    const long long n = (kMode == 0) ? g.nbricks : (long long)ctrl->n_list[which];
+    // select the list without indexing the parameter struct at run time
+    // (that would copy the struct to local memory)
+    const int *work_list = which ? s.list[1] : s.list[0];
+    const real bound0 = (real)ctrl->bound[0], bound1 = (real)ctrl->bound[1];
+    MarchStats st = {0, 0, 0, 0, 0};
+    long long it = 0, next = 0;
+    if (kMode == 1) {
+        if (lane == 0) {
+            it = (long long)atomicAdd(&ctrl->work[which], 1u);
+            next = (long long)atomicAdd(&ctrl->work[which], 1u);
+        }
+        it = __shfl_sync(FULL, it, 0);
+        next = __shfl_sync(FULL, next, 0);
+    } else {
+        it = (long long)blockIdx.x * kMarchWarps + warp;
+    }
+    while (it < n) {
+        const long long b = (kMode == 0) ? it : (long long)work_list[it];
+        unsigned long long F[kFaces];
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            F[f] = kMode == 1 ? s.inbox[b * kFaces + f] : 0ull;
+        unsigned long long m;
+        long long nb;
+        march_brick<real, kHetero, kMode, false>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+                                                 lane, m, nb, st);
+        if (kMode == 1 && m) {
+            atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
+            s.dirty[nb] = 1u;
+            st.exchanges += (unsigned long long)__popcll(m);
+        }
+        __syncwarp();
         if (kMode == 1) {
             it = next;
             if (it < n && lane == 0)
-                next = (long long)atomicAdd(&ctrl->work[which], 1u) + 0;
+                next = (long long)atomicAdd(&ctrl->work[which], 1u);
             next = __shfl_sync(FULL, next, 0);
         } else {
             it += (long long)gridDim.x * kMarchWarps;
         }
     }
-    if (kMode == 1) {
-        st_exch = __reduce_add_sync(FULL, (unsigned)st_exch);
-        if (lane == 0 && st_marches) {
-            atomicAdd(&ctrl->marches, st_marches);
-            atomicAdd(&ctrl->rounds, st_rounds);
-            atomicAdd(&ctrl->accepted, st_acc);
-            atomicAdd(&ctrl->exchanges, st_exch);
+    if (kMode == 1)
+        flush_stats(ctrl, st, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent restart: one launch marches every brick of a restart to the
+// bound until no brick has unconsumed halo changes.  Bricks wait in a ring
+// queue; a brick is in the queue or being marched at most once at a time
+// (queued[b] = 1 from the push until its march ends), so a brick always has a
+// single writer.  A march that changes boundary cells ORs them into the
+// neighbour's change masks after a fence and pushes the neighbour if it can
+// claim queued[nb]; a brick that ends its march clears queued[b] and pushes
+// itself again if masks arrived meanwhile.  `pending` counts bricks pushed and
+// not yet done; the launch ends when it reaches zero.  Every wait is bounded:
+// past the limit the kernel sets ERR_SPIN and returns.
+// ---------------------------------------------------------------------------
+
+// Waits give up after kSpinLimitNs nanoseconds of device time.
+constexpr unsigned long long kSpinLimitNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long device_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
+
+// Push brick b (the caller has claimed queued[b] and counted it in pending).
+__device__ __forceinline__ bool queue_push(Control *c, unsigned long long *q, unsigned long long cap,
+                                           long long b)
+{
+    const unsigned long long t = atomicAdd(&c->q_tail, 1ull);
+    const unsigned long long v = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
+    unsigned long long *slot = q + (t % cap);
+    const unsigned long long t0 = device_ns();
+    for (;;) {
+        if (atomicCAS(slot, 0ull, v) == 0ull)
+            return true;
+        if (device_ns() - t0 > kSpinLimitNs || (vload((const int *)&c->error) & ERR_SPIN))
+            break;
+        __nanosleep(32);
+    }
+    atomicOr(&c->error, ERR_SPIN);
+    return false;
+}
+
+// Pop a brick: -1 when the restart is complete (or on a timeout).  Each
+// caller takes a ticket from q_head and waits on its own slot, so idle warps
+// poll distinct lines with a growing back-off instead of racing on the head.
+// pending == 0 means that no push is in flight or to come, so a ticket whose
+// slot is still empty then ends the caller's loop.  The time limit counts from
+// the last push seen anywhere.
+__device__ __forceinline__ long long queue_pop(Control *c, unsigned long long *q,
+                                               unsigned long long cap)
+{
+    const unsigned long long h = atomicAdd(&c->q_head, 1ull);
+    unsigned long long *slot = q + (h % cap);
+    const unsigned long long want = h & 0xffffffffull;
+    unsigned long long t0 = device_ns(), seen = vload(&c->q_tail);
+    unsigned ns = 64;
+    for (;;) {
+        unsigned long long v = vload(slot);
+        if (v != 0ull && (v >> 32) == want) {
+            atomicExch(slot, 0ull);
+            return (long long)(v & 0xffffffffull) - 1;
+        }
+        if (vload(&c->pending) == 0) {
+            v = vload(slot);
+            if (v != 0ull && (v >> 32) == want) {
+                atomicExch(slot, 0ull);
+                return (long long)(v & 0xffffffffull) - 1;
+            }
+            return -1;
+        }
+        if (vload(&c->error) & ERR_SPIN)
+            return -1;
+        const unsigned long long now = device_ns(), tail = vload(&c->q_tail);
+        if (tail != seen) {
+            seen = tail;
+            t0 = now;
+        } else if (now - t0 > kSpinLimitNs) {
+            break;
+        }
+        __nanosleep(ns);
+        if (ns < 2048)
+            ns <<= 1;
+    }
+    atomicOr(&c->error, ERR_SPIN);
+    return -1;
+}
+
+template <typename real, bool kHetero>
+__global__ void __launch_bounds__(kMarchWarps * 32, 4)
+    k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    Control *ctrl = s.ctrl;
+    if (ctrl->done)
+        return;
+    const real bound0 = (real)ctrl->bound[0], bound1 = (real)ctrl->bound[1];
+    const unsigned long long cap = (unsigned long long)g.nbricks;
+    unsigned long long *q = s.queue;
+    MarchStats st = {0, 0, 0, 0, 0};
+    for (;;) {
+        long long b = -1;
+        if (lane == 0)
+            b = queue_pop(ctrl, q, cap);
+        b = __shfl_sync(FULL, b, 0);
+        if (b < 0)
+            break;
+        // take the changes flagged so far (later ones re-queue the brick)
+        unsigned long long mine = 0;
+        if (lane < kFaces)
+            mine = atomicExch(&s.fresh[b * kFaces + lane], 0ull);
+        __threadfence();
+        unsigned long long F[kFaces];
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            F[f] = __shfl_sync(FULL, mine, f);
+        unsigned long long m;
+        long long nb;
+        march_brick<real, kHetero, 1, true>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+                                            lane, m, nb, st);
+        // publish the write-back before flagging anything
+        __threadfence();
+        __syncwarp();
+        if (m) {
+            atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
+            st.exchanges += (unsigned long long)__popcll(m);
+            // the mask must be visible before the claim: a brick that ends
+            // its march clears its flag and then re-reads its masks
+            __threadfence();
+            if (atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
+                atomicAdd(&ctrl->pending, 1);
+                queue_push(ctrl, q, cap, nb);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            // end of the march: let neighbours queue the brick again, and do
+            // it here if changes arrived while it ran
+            atomicExch(&s.queued[b], 0u);
+            __threadfence();
+            bool again = false;
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f)
+                again = again || (vload(&s.fresh[b * kFaces + f]) != 0ull);
+            if (again && atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
+                atomicAdd(&ctrl->pending, 1);
+                queue_push(ctrl, q, cap, b);
+            }
+            __threadfence();
+            atomicAdd(&ctrl->pending, -1);
+        }
+        __syncwarp();
+    }
+    flush_stats(ctrl, st, lane);
+}
+
+// Seed the queue of a restart: bricks with a BAND cell at or below the bound.
+template <typename real>
+__global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, unsigned *queued,
+                       unsigned long long *q)
+{
+    if (ctrl->done)
+        return;
+    const double bd0 = ctrl->bound[0], bd1 = ctrl->bound[1];
+    const int lane = threadIdx.x & 31;
+    for (long long b0 = blockIdx.x * (long long)blockDim.x; b0 < g.nbricks;
+         b0 += (long long)gridDim.x * blockDim.x) {
+        const long long b = b0 + threadIdx.x;
+        bool sel = false;
+        if (b < g.nbricks) {
+            const double m0 = (double)bmin[2 * b], m1 = (double)bmin[2 * b + 1];
+            sel = (m0 < CUDART_INF && m0 <= bd0) || (m1 < CUDART_INF && m1 <= bd1);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, sel);
+        if (ball == 0u)
+            continue;
+        unsigned long long basepos = 0;
+        if (lane == 0) {
+            basepos = atomicAdd(&ctrl->q_tail, (unsigned long long)__popc(ball));
+            atomicAdd(&ctrl->pending, __popc(ball));
+        }
+        basepos = __shfl_sync(0xffffffffu, basepos, 0);
+        if (sel) {
+            const unsigned long long t = basepos + __popc(ball & ((1u << lane) - 1u));
+            queued[b] = 1u;
+            q[t % (unsigned long long)g.nbricks] = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
         }
     }
 }
@@ -819,6 +1107,9 @@ __global__ void k_control(Control *c, double width, double stride, long long max
     c->n_list[1] = 0u;
     c->work[0] = 0u;
     c->work[1] = 0u;
+    c->q_head = 0ull;
+    c->q_tail = 0ull;
+    c->pending = 0;
 }
 
 // Work lists: list 0 = bricks with a BAND cell at or below the bound or with
@@ -843,8 +1134,13 @@ __global__ void k_select(Geom g, const real *__restrict__ bmin, unsigned *dirty,
         if (b < g.nbricks) {
             dty = dirty[b] != 0u;
             sel = dty;
-            if (which == 0)
-                sel = sel || (double)bmin[2 * b] <= bd0 || (double)bmin[2 * b + 1] <= bd1;
+            if (which == 0) {
+                // a brick takes part when it has a BAND cell at or below the
+                // bound (an empty side has bound +inf, and so do the minima
+                // of bricks without BAND cells)
+                const double m0 = (double)bmin[2 * b], m1 = (double)bmin[2 * b + 1];
+                sel = sel || (m0 < CUDART_INF && m0 <= bd0) || (m1 < CUDART_INF && m1 <= bd1);
+            }
         }
         if (sel) {
 #pragma unroll
@@ -873,11 +1169,13 @@ __global__ void k_reset_control(Control *c)
     const unsigned long long INF_BITS = 0x7ff0000000000000ull;
     c->minbits[0] = INF_BITS;
     c->minbits[1] = INF_BITS;
-    c->marches = c->rounds = c->exchanges = c->accepted = 0ull;
+    c->marches = c->rounds = c->exchanges = c->accepted = c->solves = 0ull;
     c->bound[0] = c->bound[1] = 0.0;
     c->dirty_count = 0u;
     c->n_list[0] = c->n_list[1] = 0u;
     c->work[0] = c->work[1] = 0u;
+    c->q_head = c->q_tail = 0ull;
+    c->pending = 0;
     c->done = 0;
     c->error = 0;
     c->restart = 0;
@@ -1012,6 +1310,21 @@ int grid_for(long long n, int threads, int cap)
 template <typename real>
 size_t march_smem() { return sizeof(WarpTile<real>) * kMarchWarps; }
 
+// Trace: restart, phase and list length of a march launch.
+__global__ void k_trace(const Control *c, int which, int phase, int *out)
+{
+    out[0] = c->done ? -1 : c->restart;
+    out[1] = phase;
+    out[2] = c->done ? 0 : (int)c->n_list[which];
+}
+
+__global__ void k_trace_seed(const Control *c, int *out)
+{
+    out[0] = c->done ? -1 : c->restart;
+    out[1] = 0;
+    out[2] = c->done ? 0 : (int)c->q_tail;
+}
+
 __global__ void k_reset_list(Control *c, int which)
 {
     if (c->done)
@@ -1022,7 +1335,7 @@ __global__ void k_reset_list(Control *c, int which)
 
 template <typename real>
 cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
-                         cudaStream_t st, cudaEvent_t *ev)
+                         cudaStream_t st, cudaEvent_t *ev, int *trace)
 {
     const int rb = grid_for(g.nbricks, 256, 4096);
     const bool het = s.spd != nullptr;
@@ -1030,12 +1343,28 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
+    if (p.schedule == kSchedulePersistent) {
+        k_seed<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.ctrl, s.queued, s.queue);
+        if (trace)
+            k_trace_seed<<<1, 1, 0, st>>>(s.ctrl, trace);
+        if (ev)
+            cudaEventRecord(ev[0], st);
+        if (het)
+            k_march_persistent<real, true><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        else
+            k_march_persistent<real, false><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        if (ev)
+            cudaEventRecord(ev[1], st);
+        return cudaGetLastError();
+    }
     for (int pass = 0; pass <= p.passes; ++pass) {
         const int which = pass == 0 ? 0 : 1;
         if (pass >= 2)
             k_reset_list<<<1, 1, 0, st>>>(s.ctrl, 1);
         k_select<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.fresh, s.inbox,
                                            s.ctrl, s.list[which], which);
+        if (trace)
+            k_trace<<<1, 1, 0, st>>>(s.ctrl, which, pass, trace + 3 * pass);
         if (ev)
             cudaEventRecord(ev[2 * pass], st);
         if (het)
@@ -1070,6 +1399,8 @@ int configure_march()
     cudaFuncSetAttribute(k_march<real, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_march<real, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_march<real, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march_persistent<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march_persistent<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1>, kMarchWarps * 32, sm);
     return n > 0 ? n : 1;
@@ -1130,9 +1461,10 @@ cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
 }
 
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
-                           cudaStream_t st, cudaEvent_t *ev)
+                           cudaStream_t st, cudaEvent_t *ev, int *trace)
 {
-    return dtype == 1 ? restart_impl<double>(g, s, p, st, ev) : restart_impl<float>(g, s, p, st, ev);
+    return dtype == 1 ? restart_impl<double>(g, s, p, st, ev, trace)
+                      : restart_impl<float>(g, s, p, st, ev, trace);
 }
 
 cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st)

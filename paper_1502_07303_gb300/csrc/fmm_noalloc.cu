@@ -51,7 +51,9 @@ constexpr size_t kOffInbox = align256(kOffFresh + kFaces * kNoAllocMaxBricks * s
 constexpr size_t kOffDirty = align256(kOffInbox + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
 constexpr size_t kOffList0 = align256(kOffDirty + kNoAllocMaxBricks * sizeof(unsigned));
 constexpr size_t kOffList1 = align256(kOffList0 + kNoAllocMaxBricks * sizeof(int));
-constexpr size_t kOffCtrl = align256(kOffList1 + kNoAllocMaxBricks * sizeof(int));
+constexpr size_t kOffQueue = align256(kOffList1 + kNoAllocMaxBricks * sizeof(int));
+constexpr size_t kOffQueued = align256(kOffQueue + kNoAllocMaxBricks * sizeof(unsigned long long));
+constexpr size_t kOffCtrl = align256(kOffQueued + kNoAllocMaxBricks * sizeof(unsigned));
 constexpr size_t kScratchBytes = align256(kOffCtrl + sizeof(Control));   // about 2.4 MiB
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -147,6 +149,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     s.dirty = (unsigned *)(base + kOffDirty);
     s.list[0] = (int *)(base + kOffList0);
     s.list[1] = (int *)(base + kOffList1);
+    s.queue = (unsigned long long *)(base + kOffQueue);
+    s.queued = (unsigned *)(base + kOffQueued);
     s.ctrl = (Control *)(base + kOffCtrl);
     s.spd = nullptr;
     s.tape = nullptr;
@@ -162,6 +166,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
+    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
     if (p.passes > 64)
         return error(FMM_ERR_INVALID, "exchange_passes must be at most 64");
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
@@ -185,6 +190,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     NA_CUDA(launch_reset_control(s, st));
     NA_CUDA(cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     NA_CUDA(cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    NA_CUDA(cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
+    NA_CUDA(cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     NA_CUDA(launch_load_speed(dt, g, s, p.h, nullptr, 1.0, st));
     NA_CUDA(launch_init_reinit(dt, g, s, p, phi0, st));
     NA_CUDA(launch_front_init(dt, g, s, p, st));
@@ -196,7 +203,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     long long batch = 1;
     for (;;) {
         for (long long r = 0; r < batch; ++r)
-            NA_CUDA(launch_restart(dt, g, s, p, st, nullptr));
+            NA_CUDA(launch_restart(dt, g, s, p, st, nullptr, nullptr));
         NA_CUDA(cudaMemcpyAsync(&c, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
         NA_CUDA(cudaStreamSynchronize(st));
         if (c.done)
@@ -213,5 +220,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
         return error(FMM_ERR_TIMEOUT, "a brick march exceeded its round limit");
     if (c.error & ERR_RESTARTS)
         return error(FMM_ERR_TIMEOUT, "the restart limit was reached before termination");
+    if (c.error & ERR_SPIN)
+        return error(FMM_ERR_TIMEOUT, "a bounded wait of the persistent march gave up");
     return FMM_OK;
 }

@@ -21,7 +21,8 @@ TAG_FAR, TAG_BAND, TAG_KNOWN, TAG_FIX = 0, 1, 2, 3
 
 EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
-            "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch")
+            "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch",
+            "fmm_get_trace")
 
 
 class FmmConfig(ctypes.Structure):
@@ -31,7 +32,8 @@ class FmmConfig(ctypes.Structure):
                 ("stride", ctypes.c_double), ("bucket", ctypes.c_double),
                 ("ctas", ctypes.c_int32), ("timeout_s", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p),
-                ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32)]
+                ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
@@ -40,11 +42,17 @@ class FmmStats(ctypes.Structure):
                 ("accepted", ctypes.c_int64), ("n_bricks", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("march_launches", ctypes.c_int64),
                 ("march_ms", ctypes.c_double), ("adjoint_iterations", ctypes.c_int64),
-                ("error_flags", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("error_flags", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("cell_solves", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: (float(getattr(self, k)) if k == "march_ms" else int(getattr(self, k)))
                 for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class FmmTraceEntry(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("phase", ctypes.c_int32),
+                ("bricks", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class FmmError(RuntimeError):
@@ -84,9 +92,10 @@ def load(path: str | None = None):
     lib.fmm_create_batch.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(FmmConfig),
                                      ctypes.POINTER(vp)]
     lib.fmm_reinit_batch.argtypes = [vp, vp, vp, vp]
+    lib.fmm_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
               "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
-              "fmm_create_batch", "fmm_reinit_batch"):
+              "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -126,7 +135,7 @@ class Solver:
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
                  max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
-                 stream=None):
+                 schedule=0, stream=None):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
@@ -145,6 +154,7 @@ class Solver:
         cfg.timeout_s = int(timeout_s)
         cfg.time_kernels = 1 if time_kernels else 0
         cfg.exchange_passes = int(exchange_passes)
+        cfg.schedule = int(schedule)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)
@@ -211,6 +221,15 @@ class Solver:
         self._check(self.lib.fmm_get_stats(self.handle, ctypes.byref(st)))
         return st.as_dict()
 
+    def trace(self):
+        """Per march launch of the last solve: (restart, phase, bricks, ms);
+        needs time_kernels=True."""
+        n = ctypes.c_int64(0)
+        self._check(self.lib.fmm_get_trace(self.handle, None, 0, ctypes.byref(n)))
+        buf = (FmmTraceEntry * max(n.value, 1))()
+        self._check(self.lib.fmm_get_trace(self.handle, buf, n.value, ctypes.byref(n)))
+        return [(e.restart, e.phase, e.bricks, e.ms) for e in buf[: n.value]]
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.fmm_destroy(self.handle)
@@ -252,7 +271,7 @@ class Batch:
 
     def __init__(self, shapes, hs, dtype=torch.float32, width=math.inf, stride=0.0, bucket=0.0,
                  exchange_passes=0, ctas=0, max_restarts=0, timeout_s=0, time_kernels=False,
-                 stream=None):
+                 schedule=0, stream=None):
         self.lib = load()
         self.code, self.dtype = _dtype_code(dtype)
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
@@ -271,6 +290,7 @@ class Batch:
         cfg.max_restarts = int(max_restarts)
         cfg.timeout_s = int(timeout_s)
         cfg.time_kernels = 1 if time_kernels else 0
+        cfg.schedule = int(schedule)
         cfg.stream = _stream_handle(stream)
         handle = ctypes.c_void_p()
         rc = self.lib.fmm_create_batch(n, dims.ctypes.data, hh.ctypes.data, ctypes.byref(cfg),

@@ -138,10 +138,20 @@ def test_reinit_single_sphere_64(fmm, oracle):
 
 @pytest.mark.parametrize("stride", [0.5, 1.0, 2.0, 3.5, math.inf])
 @pytest.mark.parametrize("bucket", [1.0, math.inf])
-def test_stride_and_bucket_do_not_change_the_result(fmm, oracle, stride, bucket):
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_stride_bucket_schedule_do_not_change_the_result(fmm, oracle, stride, bucket, schedule):
     p = wl.random_spheres(shape=(40, 40, 40), count=5, seed=11)
-    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", stride=stride, bucket=bucket)
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", stride=stride, bucket=bucket,
+                              schedule=schedule)
     compare(T, G, ref, "f64")
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_phased_schedule_heterogeneous(fmm, oracle, dt):
+    p = wl.fourier_sources(n=33, n_sources=4, n_receivers=8, seed=5)
+    T, G, ref, st = run_sources(fmm, oracle, p.shape, p.h, p.sources, p.speed, dt, schedule=1,
+                                exchange_passes=1)
+    compare(T, G, ref, dt)
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
@@ -152,12 +162,13 @@ def test_narrow_band_width(fmm, oracle, dt):
     compare(T, G, ref, dt, width=width)
 
 
-def test_single_brick_infinite_stride_two_restarts(fmm, oracle):
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_single_brick_infinite_stride_two_restarts(fmm, oracle, schedule):
     """Sec. 5.3: with stride = inf one subdomain finishes in two restarts (the
     second only finds nothing left to do)."""
     shape = (8, 8, 8)
     T, G, ref, st = run_sources(fmm, oracle, shape, 1.0 / 8, [(1, 2, 3)], None, "f64",
-                                stride=math.inf)
+                                stride=math.inf, schedule=schedule)
     compare(T, G, ref, "f64")
     assert st["restarts"] == 2
 
@@ -167,7 +178,8 @@ def test_restarts_scale_inversely_with_stride(fmm, oracle):
     p = wl.point_source(48)
     nr = {}
     for stride in (1.0, 4.0):
-        with fmm.Solver(p.shape, p.h, dtype=torch.float64, sources=p.sources, stride=stride) as s:
+        with fmm.Solver(p.shape, p.h, dtype=torch.float64, sources=p.sources, stride=stride,
+                        schedule=1) as s:
             s.solve()
             nr[stride] = s.stats()["restarts"]
     assert nr[1.0] > 2.5 * nr[4.0]

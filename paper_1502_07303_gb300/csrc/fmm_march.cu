@@ -127,16 +127,36 @@ __device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
 // q = (h/F)^2.  The coefficients stay of order h, so rounding does not grow
 // with psi (in psi itself b^2 and 4ac would cancel to ~3 (psi F/h)^2 ulp).
 // The causality test psi_i < t is delta_i < u.  q is the cell's speed term.
+//
+// The per-axis values are sorted once (a stable sort, so equal values keep
+// the lower axis first and the higher axis is dropped first).  The smallest
+// has delta = 0, so only the other two enter S = sum delta_i and
+// Q = sum delta_i^2 (a dropped axis contributes 0): disc = S^2 - k (Q - q),
+// u = (S + sqrt(disc)) / k, causal when the largest remaining delta is below
+// u.  All lanes of a warp evaluate their full set together; a lane whose full
+// set is not causal (about 1% of solves) goes round the loop again.
+template <typename real>
+__device__ __forceinline__ void cswap(real &a, unsigned &ca, real &b, unsigned &cb)
+{
+    if (lt(b, a)) {
+        const real t = a;
+        a = b;
+        b = t;
+        const unsigned c = ca;
+        ca = cb;
+        cb = c;
+    }
+}
+
 template <typename real>
 __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real q,
                                            uint8_t &set_out)
 {
     const int off[3] = {1, kTile, kTile * kTile};
-    real psi[3];
-    bool act[3];
+    const real INF = inf_v<real>();
+    real v[3];
+    unsigned code[3];
     int nd = 0;
-    unsigned cur = 0;
-    real m = inf_v<real>();
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
@@ -145,68 +165,58 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
             d = -1;
         if (lt(vp, Tc) && (d == 0 || lt(vp, vm)))
             d = 1;
-        act[a] = d != 0;
-        psi[a] = d == 0 ? (real)0 : (d < 0 ? vm : vp);
-        if (d != 0) {
-            ++nd;
-            cur |= (d < 0 ? 1u : 2u) << (2 * a);
-            m = vmin(m, psi[a]);
-        }
+        v[a] = d == 0 ? INF : (d < 0 ? vm : vp);
+        code[a] = d == 0 ? 0u : (d < 0 ? 1u : 2u) << (2 * a);
+        nd += d != 0;
     }
-    real del[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        del[a] = act[a] ? psi[a] - m : (real)0;
+    // stable sort of three (adjacent compare-exchange, strict less-than)
+    cswap(v[0], code[0], v[1], code[1]);
+    cswap(v[1], code[1], v[2], code[2]);
+    cswap(v[0], code[0], v[1], code[1]);
+    set_out = 0;
+    if (nd == 0)
+        return INF;
+    const real m = v[0];
+    real d1 = nd >= 2 ? v[1] - m : (real)0;
+    real d2 = nd >= 3 ? v[2] - m : (real)0;
 #pragma unroll 1
     for (; nd != 0; --nd) {
-        real S = 0, Q = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (act[a]) {
-                S += del[a];
-                Q += del[a] * del[a];
-            }
-        const real k = (real)nd;
-        const real disc = S * S - k * (Q - q);
+        const real S = d1 + d2;
+        const real Q = fma(d2, d2, d1 * d1);
+        const real k = nd == 3 ? (real)3 : (nd == 2 ? (real)2 : (real)1);
+        const real disc = fma(-k, Q - q, S * S);
         if (!lt(disc, (real)0)) {
-            const real inv_k = nd == 1 ? (real)1 : (nd == 2 ? (real)0.5 : (real)(1.0 / 3.0));
+            const real inv_k = nd == 3 ? (real)(1.0 / 3.0) : (nd == 2 ? (real)0.5 : (real)1);
             const real u = (S + vsqrt(disc)) * inv_k;
-            bool causal = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                causal = causal && (!act[a] || lt(del[a], u));
-            if (causal) {
-                set_out = (uint8_t)cur;
+            const real dmax = nd == 3 ? d2 : d1;   // 0 when nd == 1
+            if (lt(dmax, u)) {
+                set_out = (uint8_t)(code[0] | (nd >= 2 ? code[1] : 0u) | (nd == 3 ? code[2] : 0u));
                 return m + u;
             }
         }
-        // drop the axis with the largest psi still in the stencil (ties: the
-        // higher axis index)
-        int j = -1;
-        real dj = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (act[a] && (j < 0 || !lt(del[a], dj))) {
-                j = a;
-                dj = del[a];
-            }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == j)
-                act[a] = false;
-        cur &= ~(3u << (2 * j));
+        // drop the largest remaining value
+        if (nd == 3)
+            d2 = (real)0;
+        else
+            d1 = (real)0;
     }
-    set_out = 0;
-    return inf_v<real>();
+    return INF;
 }
 
-template <typename real>
-__device__ __forceinline__ real warp_min(real v)
+// Warp minimum of non-negative values (or +inf): their bit patterns order
+// like the values, so the integer reductions of the warp do it exactly (a
+// double in two steps, high word then low word).
+__device__ __forceinline__ float warp_min(float v)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    return __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(v)));
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(b >> 32));
+    const unsigned lo =
+        __reduce_min_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0xffffffffu);
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
 // ---------------------------------------------------------------------------
@@ -398,6 +408,13 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
 // ---------------------------------------------------------------------------
 
 constexpr int kMarchWarps = 4;   // bricks in flight per CTA
+#ifndef FMM_MARCH_BLOCKS_F32
+#define FMM_MARCH_BLOCKS_F32 7
+#endif
+// Resident CTAs per SM the march kernels are compiled for (registers): the
+// fp64 tile (12 KB a warp) already limits fp64 to four.
+template <typename real>
+constexpr int march_min_blocks() { return sizeof(real) == 4 ? FMM_MARCH_BLOCKS_F32 : 4; }
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename real>
@@ -573,15 +590,19 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
     int rounds = 0;
     real m0 = INF, m1 = INF;
     // Settled cells: KNOWN cells at or below the band minimum of their side.
-    // No later acceptance in this march can lower them: the band minimum
-    // never falls within a march (a value computed from an accepted
-    // neighbour v is a causal root, so it exceeds v, and v is at least the
-    // minimum), every accepted value is at least that minimum, and an update
-    // from an upwind value v never goes below v.  They are left out of the
-    // solves.  pend: cells accepted at or below lim (pl0, pl1) that settle once
-    // the minimum of their side reaches it.
+    // An accepted value is at least the band minimum of its round, and an
+    // update from an upwind value v never goes below v, so while the minimum
+    // does not fall no later acceptance can lower a settled cell and the
+    // cell is left out of the solves.  The minimum normally only rises (a
+    // value computed from an accepted neighbour v is a causal root above v),
+    // but a halo value staged before its change flag arrived (written by a
+    // neighbour brick during this march) can let a relaxed cell drop below it;
+    // when the minimum of a side falls, that side's settled cells are
+    // released.  pend: cells accepted at or below the largest lim so far
+    // (pl0, pl1) that settle once the minimum of their side reaches it.
     unsigned settled = 0, pend = 0;
-    real pl0 = INF, pl1 = INF;
+    real pl0 = (real)0, pl1 = (real)0;
+    real mp0 = (real)0, mp1 = (real)0;   // band minima of the previous round
     for (;;) {
         // compact the cells to solve (warp prefix sum of the lane counts)
         const int cnt = __popc(relax);
@@ -640,6 +661,12 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         m1 = warp_min(l1);
         if (kMode == 0)
             break;
+        if (lt(m0, mp0))
+            settled &= ~neg;
+        if (lt(m1, mp1))
+            settled &= neg;
+        mp0 = m0;
+        mp1 = m1;
         if (rounds == 0) {
             // cells that were KNOWN when the march began
             for (unsigned m = known & ~settled; m; m &= m - 1u) {
@@ -683,8 +710,9 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             break;
         acc_any |= acc;
         pend |= acc;
-        pl0 = lim0;
-        pl1 = lim1;
+        // a falling minimum lowers lim, so keep the largest lim of the pending cells
+        pl0 = lt(pl0, lim0) ? lim0 : pl0;
+        pl1 = lt(pl1, lim1) ? lim1 : pl1;
         st.accepted += (unsigned long long)nacc;
         if (++rounds > p.max_rounds) {
             if (lane == 0)
@@ -786,7 +814,7 @@ __device__ __forceinline__ void flush_stats(Control *ctrl, MarchStats &st, int l
 // a shared counter) with the change masks the select kernel moved to the
 // inbox; changes are flagged in the neighbours' live masks and dirty flags.
 template <typename real, bool kHetero, int kMode>
-__global__ void __launch_bounds__(kMarchWarps * 32, 4)
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -935,7 +963,7 @@ __device__ __forceinline__ long long queue_pop(Control *c, unsigned long long *q
 }
 
 template <typename real, bool kHetero>
-__global__ void __launch_bounds__(kMarchWarps * 32, 4)
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1058,8 +1086,8 @@ __global__ void k_reduce(Geom g, const real *__restrict__ bmin, const unsigned *
         m1 = fmin(m1, (double)bmin[2 * b + 1]);
         cnt += dirty[b] != 0u;
     }
-    m0 = warp_min<double>(m0);
-    m1 = warp_min<double>(m1);
+    m0 = warp_min(m0);
+    m1 = warp_min(m1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);

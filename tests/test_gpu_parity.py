@@ -104,6 +104,22 @@ def test_fourier_speed(fmm, oracle, n, dt):
     compare(T, G, ref, dt)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_fourier_speed_many_seeds(fmm, oracle, schedule):
+    """Twelve seeds, each solved twice: brick marches run concurrently, so the
+    order in which halo values and their change flags reach a brick differs
+    from run to run; every run must reach the oracle's fixed point."""
+    for seed in range(12):
+        p = wl.fourier_sources(n=41, n_sources=4, n_receivers=8, seed=seed)
+        ref = oracle.solve_sources(p.shape, p.sources, p.h, speed=p.speed)
+        sp = _dev(p.speed, "f64")
+        for _ in range(2):
+            with fmm.Solver(p.shape, p.h, dtype=torch.float64, speed=sp, sources=p.sources,
+                            schedule=schedule) as s:
+                T, G = s.solve()
+            compare(_host(T), _host(G), ref, "f64")
+
+
 @pytest.mark.parametrize("case", [4, 5])
 def test_paper_speed_cases(fmm, oracle, case):
     """Sec. 5.1 cases 4 and 5 (Eq. (9), (10)): point source at the centre."""

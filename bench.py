@@ -53,9 +53,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record():
-    """Bytes per point of the march kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
+def traffic_record(kernel):
+    """DRAM bytes per finalised point of the march kernel from the committed
+    ncu summary, valid only for that kernel while its source is unchanged."""
     path = os.path.join(ROOT, "profiles", "k_march_traffic.txt")
     src = os.path.join(ROOT, "paper_1502_07303_gb300", "csrc", "fmm_march.cu")
     try:
@@ -65,7 +65,7 @@ def traffic_record():
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") != sha:
+        if rec.get("source_sha256_16") != sha or rec.get("kernel") != kernel:
             return None
         return float(rec["dram_bytes_per_point"])
     except Exception:
@@ -218,11 +218,11 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream):
+def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream, params):
     """Device-timed solves: CUDA events around each solve on the solve's
     stream, L2 flushed (256 MiB write) before every step, outside the events."""
     shape = p.shape
-    s = fmm.Solver(shape, p.h, dtype=dtype, time_kernels=True, stream=stream)
+    s = fmm.Solver(shape, p.h, dtype=dtype, time_kernels=True, stream=stream, **params)
     T_out = torch.empty(shape, dtype=dtype, device="cuda")
     G_out = torch.empty(shape, dtype=torch.uint8, device="cuda")
     for _ in range(warmup):
@@ -250,11 +250,11 @@ def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream):
             "T": T_out}
 
 
-def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream):
+def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream, params):
     """The user's call with host buffers: pinned phi0 -> device, solve, psi
     back to pinned host memory, all inside the timed region of every step."""
     shape = p.shape
-    s = fmm.Solver(shape, p.h, dtype=dtype, stream=stream)
+    s = fmm.Solver(shape, p.h, dtype=dtype, stream=stream, **params)
     phi_dev = torch.empty(shape, dtype=dtype, device="cuda")
     T_out = torch.empty(shape, dtype=dtype, device="cuda")
     T_host = torch.empty(shape, dtype=dtype, pin_memory=True)
@@ -373,6 +373,19 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     pts = p.n_points
 
+    # restart parameters: the library's autotuner on this workload, before
+    # any timed region (persistent schedule over strides, phased at default)
+    from paper_1502_07303_gb300 import autotune
+    tuned, tune_tables = {}, {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        if args.params is not None:
+            tuned[name] = dict(args.params)
+            continue
+        best, best_ms, table = autotune.tune(p, dt, kind="reinit", search=autotune.QUICK, reps=2,
+                                             save=False, stream=stream)
+        tuned[name] = best or {}
+        tune_tables[name] = [[c, None if ms is None else round(ms, 3)] for c, ms in table]
+
     # fp32: the headline
     barrier(pg)
     torch.cuda.synchronize()
@@ -380,7 +393,8 @@ def run_gpu(args):
     if sampler:
         sampler.start()
     t_wall = time.perf_counter()
-    r32 = measure(fmm, torch, phi32, p, torch.float32, args.steps, args.warmup, flush, stream)
+    r32 = measure(fmm, torch, phi32, p, torch.float32, args.steps, args.warmup, flush, stream,
+                  tuned["f32"])
     torch.cuda.synchronize()
     barrier(pg)
     wall_ms = 1e3 * (time.perf_counter() - t_wall)
@@ -388,15 +402,23 @@ def run_gpu(args):
     ms32 = max_over_ranks(pg, r32["ms"])
     total_pts = sum_over_ranks(pg, float(pts))
     value = total_pts / (ms32 / 1e3) / 1e9
+    if args.part == "f32":
+        if rank == 0:
+            print(json.dumps({"part": "f32", "value": value, "unit": UNIT, "ms_per_step": ms32,
+                              "params": tuned["f32"], "march_ms": r32["march_ms"],
+                              "march_launches": r32["march_launches"],
+                              "stats": r32["stats"]}), flush=True)
+        return 0
 
     # fp64 on the same workload
-    r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream)
+    r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream,
+                  tuned["f64"])
     ms64 = max_over_ranks(pg, r64["ms"])
 
     # end to end through the public API with host buffers (fp32)
     phi_host = phi32.cpu().pin_memory()
     e2e_ms, h2d, d2h = measure_e2e(fmm, torch, phi_host, p, torch.float32, args.steps,
-                                   args.warmup, stream)
+                                   args.warmup, stream, tuned["f32"])
     e2e_ms = max_over_ranks(pg, e2e_ms)
     e2e_value = total_pts / (e2e_ms / 1e3) / 1e9
 
@@ -409,14 +431,15 @@ def run_gpu(args):
     peak, peak_kind = peaks()
 
     def roofline(r, dt):
+        kernel = "k_march" if tuned[dt].get("schedule", 0) == 1 else "k_march_persistent"
         launches = max(r["march_launches"], 1.0)
         avg_launch_s = r["march_ms"] / launches / 1e3
         alg_per_launch = ALG_BYTES[dt] * pts / launches
         achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-        bpp = traffic_record() if dt == "f32" else None
+        bpp = traffic_record(kernel) if dt == "f32" else None
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (bpp * pts / launches) if bpp else None,
-                "kernel": "k_march", "peak_kind": peak_kind,
+                "kernel": kernel, "peak_kind": peak_kind,
                 "avg_launch_us": 1e3 * r["march_ms"] / launches,
                 "launches_per_step": r["march_launches"],
                 "share_of_step": r["march_ms"] / r["ms"]}
@@ -429,8 +452,11 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"reinit random_spheres{N_SPHERES} {n}^3", "grid": [n, n, n],
                    "points_per_gpu": pts, "seed": SEED,
-                   "restart_params": "library defaults (fp32: stride 16h, bucket 4, 2 exchange "
-                                     "passes; fp64: stride 8h, bucket 4, 1 pass)",
+                   "restart_params": {"f32": tuned["f32"], "f64": tuned["f64"],
+                                      "chosen_by": ("given with --params" if args.params is not None
+                                                    else "autotune.QUICK on this workload before "
+                                                         "timing (ms per candidate in tune_ms)"),
+                                      "tune_ms": tune_tables},
                    "brick": 8, "l2": "flushed before every step (256 MiB write)",
                    "replicas": ws, "parallelism": "independent replicas, no collective"},
         "roofline": roofline(r32, "f32"),
@@ -447,11 +473,16 @@ def run_gpu(args):
         "adjoint": adjoint,
         "batched": batched,
         "solve_stats": {k: st[k] for k in ("restarts", "brick_marches", "march_rounds",
-                                            "exchanges", "accepted", "n_bricks")},
+                                            "exchanges", "accepted", "cell_solves", "n_bricks")},
         "wall_ms_timed_region": wall_ms,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _params(text):
+    d = json.loads(text)
+    return {k: (float(v) if k in ("stride", "bucket") else int(v)) for k, v in d.items()}
 
 
 def main():
@@ -461,6 +492,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID, help=argparse.SUPPRESS)
+    ap.add_argument("--part", default="all", choices=["all", "f32"],
+                    help="f32: only the fp32 timed solves (for profiling)")
+    ap.add_argument("--params", type=_params, default=None,
+                    help="restart parameters as JSON (skips the autotuner), e.g. "
+                         "'{\"schedule\": 2, \"stride\": \"inf\"}'")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -166,10 +166,12 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness);
 /*
  * fmm_create_batch -- a solver for n_grids independent grids of uneven sizes
  * that are reinitialised together (speed F = 1): the bricks of all grids are
- * packed into one brick array and every phase of the restart loop of
- * Algorithm 16 is one launch over one shared work list; no data crosses from
- * one grid to another.  The restart bound is common to all grids (Algorithm
- * 16 is correct for any bound; a grid whose front is done simply has no work).
+ * packed into one brick array, and with the persistent schedule (the
+ * default) every restart of Algorithm 16 is one launch that marches bricks
+ * of all grids from one shared queue (phased: one launch per phase over one
+ * shared work list); a neighbour table stops data at the border of a grid.
+ * The restart bound is common to all grids (Algorithm 16 is correct for any
+ * bound; a grid whose front is done simply has no work).
  *   dims : host, 3 * n_grids int64 (nx, ny, nz of every grid)
  *   h    : host, n_grids spacings
  *   cfg  : dtype, width, stride (in units of the smallest h), bucket,

@@ -3,9 +3,12 @@
 The paper's only free parameter is the restart stride (Sec. 4.4, Sec. 5.1):
 it studies 0.5-3.5 h and infinity, suggests 2 h for its CPU cluster and
 advises experimenting on new platforms (Sec. 5.5).  On the GPU the stride,
-the bucket width of the local march, the number of exchange passes per
-restart and the number of CTAs of the march kernel all trade restarts
-against re-acceptance, so they are tuned together.  The brick is fixed at
+the restart schedule (persistent queue or phased passes), the bucket width
+of the local march, the number of exchange passes per restart and the
+number of CTAs of the march kernel all trade restarts against
+re-acceptance, so they are tuned together.  Many small fronts favour long
+strides (each restart ends in a tail where few bricks are left); one large
+front favours short ones (less re-acceptance).  The brick is fixed at
 8x8x8 (one warp per brick).
 
 ``tune`` times every candidate on a representative problem with CUDA events
@@ -24,12 +27,20 @@ import statistics
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                              "autotune.json")
 
+PARAMS = ("schedule", "stride", "bucket", "exchange_passes", "ctas")
+
 SEARCH = {
+    "schedule": [1, 2],
     "stride": [2.0, 4.0, 8.0, 16.0, 32.0, math.inf],
     "bucket": [1.0, 2.0, 4.0, math.inf],
-    "exchange_passes": [1, 2, 3],
+    "exchange_passes": [0],
     "ctas": [0],
 }
+
+# A short list for a quick tune (the persistent schedule over strides, the
+# phased one at its default stride).
+QUICK = ([{"schedule": 2, "stride": s, "bucket": 4.0} for s in (8.0, 16.0, 32.0, 64.0, math.inf)]
+         + [{"schedule": 1, "stride": 0.0, "bucket": 4.0}])
 
 
 def cache_path(path=None):
@@ -73,16 +84,20 @@ def params_for(kind, dtype, n_points, path=None):
     entry = load_cache(path).get(key(kind, _dtype_name(dtype), n_points))
     if not entry:
         return {}
-    return {k: entry[k] for k in ("stride", "bucket", "exchange_passes", "ctas") if k in entry}
+    return {k: entry[k] for k in PARAMS if k in entry}
 
 
 def candidates(search=None):
+    """search: a dict of value lists (the product is taken, missing keys from
+    SEARCH) or an explicit list of parameter dicts."""
+    if isinstance(search, (list, tuple)):
+        yield from (dict(c) for c in search)
+        return
     sp = dict(SEARCH)
     if search:
         sp.update(search)
-    names = ["stride", "bucket", "exchange_passes", "ctas"]
-    for vals in itertools.product(*(sp[n] for n in names)):
-        yield dict(zip(names, vals))
+    for vals in itertools.product(*(sp[n] for n in PARAMS)):
+        yield dict(zip(PARAMS, vals))
 
 
 def select_best(timings):
@@ -109,7 +124,8 @@ def _time_call(torch, fn, reps):
     return min(ts)
 
 
-def tune(problem, dtype, kind=None, search=None, reps=2, path=None, save=True, log=None):
+def tune(problem, dtype, kind=None, search=None, reps=2, path=None, save=True, log=None,
+         stream=None):
     """Time every candidate on ``problem`` (a workloads.Problem with phi0 or
     sources) and store the fastest.  Returns (best_params, best_ms, table)."""
     import torch
@@ -129,7 +145,7 @@ def tune(problem, dtype, kind=None, search=None, reps=2, path=None, save=True, l
     for params in candidates(search):
         try:
             with fmm.Solver(problem.shape, problem.h, dtype=dtype, speed=speed,
-                            sources=problem.sources, **params) as s:
+                            sources=problem.sources, stream=stream, **params) as s:
                 if phi is not None:
                     def run():
                         s.reinit(phi, T, None, want_tags=False)

@@ -33,9 +33,17 @@ def test_cache_roundtrip(tmp_path):
     assert autotune.params_for("reinit", "float64", 1000, path=path) == {}
 
 
+def test_candidate_list():
+    got = list(autotune.candidates(autotune.QUICK))
+    assert got == [dict(c) for c in autotune.QUICK]
+    assert {c["schedule"] for c in got} == {1, 2}
+    assert all(set(c) <= set(autotune.PARAMS) for c in got)
+
+
 def test_candidate_grid():
-    c = list(autotune.candidates({"stride": [2.0, 8.0], "bucket": [1.0], "exchange_passes": [1, 2]}))
-    assert len(c) == 4 and all(set(x) == {"stride", "bucket", "exchange_passes", "ctas"} for x in c)
+    c = list(autotune.candidates({"schedule": [2], "stride": [2.0, 8.0], "bucket": [1.0],
+                                  "exchange_passes": [1, 2]}))
+    assert len(c) == 4 and all(set(x) == set(autotune.PARAMS) for x in c)
 
 
 @pytest.mark.gpu

@@ -431,7 +431,8 @@ def run_gpu(args):
     peak, peak_kind = peaks()
 
     def roofline(r, dt):
-        kernel = "k_march" if tuned[dt].get("schedule", 0) == 1 else "k_march_persistent"
+        kernel = {1: "k_march", 2: "k_march_persistent"}.get(tuned[dt].get("schedule", 0),
+                                                              "k_march_continuous")
         launches = max(r["march_launches"], 1.0)
         avg_launch_s = r["march_ms"] / launches / 1e3
         alg_per_launch = ALG_BYTES[dt] * pts / launches

@@ -62,7 +62,7 @@ typedef struct {
     int32_t record_tape;   /* 1: keep the upwind sets for fmm_adjoint           */
     double width;          /* width_band (Algorithm 5/12); 0 -> +inf (full march) */
     double stride;         /* restart stride delta_s in units of h (Algorithm 16);
-                              0 -> the GB300 default (16 for FMM_F32, 8 for
+                              0 -> the GB300 default (16 for FMM_F32, 4 for
                               FMM_F64; the paper suggests 2 for its CPU
                               cluster and tuning per platform, Sec. 5.5);
                               +inf allowed                                     */
@@ -78,14 +78,21 @@ typedef struct {
     int32_t exchange_passes; /* phased schedule: exchange + march passes after
                               the first march of every restart (Algorithm 16
                               has 1); 0 -> 2 for FMM_F32, 1 for FMM_F64      */
-    int32_t schedule;      /* 0 -> persistent (the default); 1 phased: every
+    int32_t schedule;      /* 0 -> continuous (the default); 1 phased: every
                               restart is a select + march launch, then
                               exchange_passes select + march launches, as in
                               Algorithm 16; 2 persistent: one launch per
                               restart marches every brick to the bound,
                               re-queuing bricks whose halo changed until none
-                              is left                                         */
-    int32_t reserved2;
+                              is left; 3 continuous: one launch for the whole
+                              solve, the bound rises by the stride whenever
+                              few bricks are left below it, so one restart's
+                              last bricks overlap the next one's first      */
+    int32_t max_lead;      /* continuous schedule: while bricks are queued or
+                              marching, the bound stays within max_lead
+                              strides of the smallest BAND value the last scan
+                              saw (a small front cannot run ahead); 0 -> 3;
+                              large values remove the limit                   */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */

@@ -27,20 +27,23 @@ import statistics
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                              "autotune.json")
 
-PARAMS = ("schedule", "stride", "bucket", "exchange_passes", "ctas")
+PARAMS = ("schedule", "stride", "bucket", "exchange_passes", "ctas", "max_lead")
 
 SEARCH = {
-    "schedule": [1, 2],
+    "schedule": [1, 2, 3],
     "stride": [2.0, 4.0, 8.0, 16.0, 32.0, math.inf],
     "bucket": [1.0, 2.0, 4.0, math.inf],
     "exchange_passes": [0],
     "ctas": [0],
+    "max_lead": [0],
 }
 
-# A short list for a quick tune (the persistent schedule over strides, the
-# phased one at its default stride).
-QUICK = ([{"schedule": 2, "stride": s, "bucket": 4.0} for s in (8.0, 16.0, 32.0, 64.0, math.inf)]
-         + [{"schedule": 1, "stride": 0.0, "bucket": 4.0}])
+# A short list for a quick tune: the continuous schedule over strides (its
+# default lead, and without a lead limit at short strides), the persistent
+# one without restarts.
+QUICK = ([{"schedule": 3, "stride": s, "bucket": 4.0} for s in (4.0, 8.0, 16.0, 32.0)]
+         + [{"schedule": 3, "stride": s, "bucket": 4.0, "max_lead": 1 << 20} for s in (2.0, 4.0)]
+         + [{"schedule": 2, "stride": math.inf, "bucket": 4.0}])
 
 
 def cache_path(path=None):

@@ -239,8 +239,9 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     // restarts after the terminating pass only return; the march launches
     // that did work are those of every pass but the last
     const long long worked =
-        c.restart > 0 ? (long long)marches_per_restart(hd->params.passes, hd->params.schedule) * (c.restart - 1)
-                      : 0;
+        c.host_restart > 0
+            ? (long long)marches_per_restart(hd->params.passes, hd->params.schedule) * (c.host_restart - 1)
+            : 0;
     hd->stats.march_launches = worked;
     hd->stats.kernel_launches = launches + hd->pre_launches;
     hd->pre_launches = 0;
@@ -257,7 +258,7 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     if (timing && worked > 0) {
         std::vector<int> tr((size_t)worked * 3);
         FMM_CUDA(hd, cudaMemcpy(tr.data(), hd->d_trace, tr.size() * sizeof(int), cudaMemcpyDeviceToHost));
-        for (long long k = 0; k < worked; ++k) {
+        for (long long k = 0; k < worked && (size_t)(2 * k + 1) < ev_used; ++k) {
             fmm_trace_entry e;
             e.restart = tr[3 * k];
             e.phase = tr[3 * k + 1];
@@ -313,8 +314,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return fail(nullptr, FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
     if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
         return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
-    if (cfg->schedule < 0 || cfg->schedule > 2)
-        return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1 or 2");
+    if (cfg->schedule < 0 || cfg->schedule > 3)
+        return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1, 2 or 3");
     if (n_src < 0 || (n_src > 0 && !src_ijk))
         return fail(nullptr, FMM_ERR_INVALID, "bad source list");
     if (speed && !aligned16(speed))
@@ -349,9 +350,12 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     p.stride = stride_h * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
-    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
+    p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
+                 : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
+                                                        : kScheduleContinuous;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
 
     auto bail = [&](fmm_status code) {
         g_create_error = hd->err;
@@ -400,6 +404,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return bail(cuda_fail(hd, e, "cudaMallocHost"));
     const int per_sm = march_blocks_per_sm(cfg->dtype);
     s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
+    hd->params.raise_at = raise_threshold(s.march_ctas);
     fmm_status rc = load_speed(hd, speed, speed_const);
     if (rc != FMM_OK)
         return bail(rc);
@@ -587,9 +592,12 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * hmin;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
-    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
+    p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
+                 : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
+                                                        : kScheduleContinuous;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
     p.spd_term = 0.0;
     auto bail = [&](fmm_status code) {
         g_create_error = hd->err;
@@ -637,6 +645,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     s.nbr = hd->d_nbr;
     const int per_sm = march_blocks_per_sm(cfg->dtype);
     s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
+    hd->params.raise_at = raise_threshold(s.march_ctas);
     e = cudaMemcpy(hd->d_nbr, nbr.data(), nb * kFaces * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(hd->d_bgrid, bgrid.data(), nb * sizeof(int), cudaMemcpyHostToDevice);

@@ -56,8 +56,8 @@ struct Control {
     unsigned int work[2];            // next unclaimed entry of each list
     int done;
     int error;
-    int restart;
-    int pad;
+    int restart;                     // bound levels (restarts and raises)
+    int host_restart;                // restarts the host enqueued (k_control)
     // persistent march: ring queue positions and the count of bricks pushed
     // and not yet marched, each on a line of its own (they are the only
     // words every warp touches)
@@ -65,6 +65,14 @@ struct Control {
     alignas(128) unsigned long long q_tail;
     alignas(128) int pending;
     int pad2[31];
+    // continuous schedule: bound level (even = stable, odd = being raised),
+    // chunk counters of the scan for the current level, minima it saw
+    alignas(128) int epoch;
+    int scan_next;
+    int scan_done;
+    int pad3[2];
+    unsigned long long scan_min[2];
+    int pad4[22];
 };
 
 struct Geom {
@@ -84,15 +92,32 @@ struct SolveParams {
     long long max_restarts;
     int max_rounds;     // per brick march
     int passes;         // exchange + march passes after the first march
-    int schedule;       // kSchedulePhased or kSchedulePersistent
+    int schedule;       // kSchedulePhased, kSchedulePersistent or kScheduleContinuous
+    int raise_at;       // continuous schedule: raise the bound when fewer
+                        // bricks than this are queued or marching
+    double max_lead;    // continuous schedule: lead of the bound in strides
 };
 
 constexpr int kSchedulePhased = 1;
 constexpr int kSchedulePersistent = 2;
+constexpr int kScheduleContinuous = 3;
+constexpr int kMarchWarps = 4;   // bricks in flight per CTA of the march kernels
+#ifndef FMM_RAISE_DIV
+#define FMM_RAISE_DIV 2
+#endif
+// Continuous schedule: the bound rises once fewer bricks than this are queued
+// or marching (a fraction of the warps of the march launch).
+inline int raise_threshold(int march_ctas) { return march_ctas * kMarchWarps / FMM_RAISE_DIV; }
+// bricks one warp scans for the next bound (continuous schedule)
+constexpr int kScanChunk = 1024;
+inline bool one_launch_schedule(int schedule)
+{
+    return schedule == kSchedulePersistent || schedule == kScheduleContinuous;
+}
 
 // Defaults of the restart parameters (units of h and of the bucket width),
 // measured on GB300 for 8^3 bricks.
-inline double default_stride(int dtype) { return dtype == 1 ? 8.0 : 16.0; }
+inline double default_stride(int dtype) { return dtype == 1 ? 4.0 : 16.0; }
 inline int default_passes(int dtype) { return dtype == 1 ? 1 : 2; }
 constexpr double kDefaultBucket = 4.0;
 
@@ -145,12 +170,12 @@ cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
 // per march launch (2 * (1 + passes) events).
 inline int launches_per_restart(int passes, int schedule)
 {
-    return schedule == kSchedulePersistent ? 4 : 2 + 2 * (1 + passes) + (passes - 1);
+    return one_launch_schedule(schedule) ? 4 : 2 + 2 * (1 + passes) + (passes - 1);
 }
 // march launches (timed, traced) per restart
 inline int marches_per_restart(int passes, int schedule)
 {
-    return schedule == kSchedulePersistent ? 1 : 1 + passes;
+    return one_launch_schedule(schedule) ? 1 : 1 + passes;
 }
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
                            const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev,

@@ -119,7 +119,8 @@ __device__ __forceinline__ double vsqrt(double v)
     const double y = v * r;
     return fma(0.5 * r, fma(-y, y, v), y);
 }
-__device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
+// Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance).
+__device__ __forceinline__ float vsqrt(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
 
 // The quadratic of Algorithm 11, sum_i (t - psi_i)^2 / h^2 = 1/F^2 over the
 // upwind set, is solved for the unknown shifted by the smallest upwind value
@@ -169,13 +170,13 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
         code[a] = d == 0 ? 0u : (d < 0 ? 1u : 2u) << (2 * a);
         nd += d != 0;
     }
+    set_out = 0;
+    if (nd == 0)
+        return INF;
     // stable sort of three (adjacent compare-exchange, strict less-than)
     cswap(v[0], code[0], v[1], code[1]);
     cswap(v[1], code[1], v[2], code[2]);
     cswap(v[0], code[0], v[1], code[1]);
-    set_out = 0;
-    if (nd == 0)
-        return INF;
     const real m = v[0];
     real d1 = nd >= 2 ? v[1] - m : (real)0;
     real d2 = nd >= 3 ? v[2] - m : (real)0;
@@ -407,7 +408,6 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
 // 32 lanes solve.
 // ---------------------------------------------------------------------------
 
-constexpr int kMarchWarps = 4;   // bricks in flight per CTA
 #ifndef FMM_MARCH_BLOCKS_F32
 #define FMM_MARCH_BLOCKS_F32 7
 #endif
@@ -509,6 +509,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
     real *bmin = (real *)s.bmin;
     const real INF = inf_v<real>();
     const int lx = lane & 7, lr = (lane >> 3) & 3;
+    const int tb = 111 + lx + kTile * lr;   // tile index of the lane's cell k = 0
     long long nbi[kFaces];
 #pragma unroll
     for (int f = 0; f < kFaces; ++f)
@@ -622,18 +623,21 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         // Algorithm 10/11: solve, then apply (Jacobi within 32 cells)
         for (int i0 = 0; i0 < n_items; i0 += 32) {
             const int i = i0 + lane;
-            int c = -1;
-            real cand = INF;
+            int c = -1, ti = 0;
+            real cand = INF, tc = INF;
             uint8_t cset = 0;
             if (i < n_items) {
                 c = W.list[i];
+                ti = tile_of(c);
+                tc = W.tv[c];
                 const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
-                cand = solve_cell<real>(W.kv, tile_of(c), W.tv[c], sp, cset);
+                cand = solve_cell<real>(W.kv, ti, tc, sp, cset);
             }
             __syncwarp();
-            if (c >= 0 && lt(cand, W.tv[c])) {
+            // each cell appears once in the list, so tc is still its value
+            if (c >= 0 && lt(cand, tc)) {
                 W.tv[c] = cand;
-                W.kv[tile_of(c)] = INF;
+                W.kv[ti] = INF;
                 W.tp[c] = cset;
                 atomicOr(&W.improved[c & 31], 1u << (c >> 5));
             }
@@ -696,7 +700,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             const bool ng = (neg >> k) & 1u;
             if (!lt(ng ? lim0 : lim1, v)) {
                 acc |= 1u << k;
-                W.kv[tile_of(c)] = v;
+                W.kv[tb + 40 * (k & 1) + 100 * (k >> 1)] = v;
             } else if (ng) {
                 r0 = vmin(r0, v);
             } else {
@@ -1032,6 +1036,316 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     flush_stats(ctrl, st, lane);
 }
 
+// ---------------------------------------------------------------------------
+// Continuous schedule: the restarts of Algorithm 16 without the barrier
+// between them.  One launch marches until the solve is complete.  Each march
+// takes the current bound when it starts.  Once fewer bricks than raise_at
+// are queued or marching, an idle warp raises the bound to
+// max(bound, minimum seen by the last scan) + stride (at most width) and the
+// idle warps scan the per-brick minima in chunks, pushing every brick with a
+// BAND cell at or below the new bound; a brick that ends a march with a BAND
+// cell at or below the current bound pushes itself again.  The bricks of the
+// last shell of one restart thus overlap the first bricks of the next.  epoch
+// works as a sequence lock: odd while a raise rewrites the bound and the scan
+// counters.  The solve is complete when no raise is in progress, the last
+// scan is done, nothing is queued or marching and the bound has reached width
+// on both sides.  Every wait is bounded (kSpinLimitNs without any progress).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double vloadd(const double *p) { return *(const volatile double *)p; }
+__device__ __forceinline__ unsigned long long vloadu(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+// Push, with one tail increment for the warp, the bricks b of the lanes whose
+// sel is set and that claim queued[b].
+__device__ __forceinline__ void queue_push_warp(Control *c, unsigned long long *q, unsigned long long cap,
+                                                unsigned *queued, long long b, bool sel, int lane)
+{
+    const bool mine = sel && atomicCAS(&queued[b], 0u, 1u) == 0u;
+    const unsigned ball = __ballot_sync(FULL, mine);
+    if (ball == 0u)
+        return;
+    unsigned long long t0 = 0;
+    if (lane == 0) {
+        atomicAdd(&c->pending, __popc(ball));
+        t0 = atomicAdd(&c->q_tail, (unsigned long long)__popc(ball));
+    }
+    t0 = __shfl_sync(FULL, t0, 0);
+    if (mine) {
+        const unsigned long long t = t0 + __popc(ball & ((1u << lane) - 1u));
+        const unsigned long long v = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
+        unsigned long long *slot = q + (t % cap);
+        const unsigned long long ts = device_ns();
+        while (atomicCAS(slot, 0ull, v) != 0ull) {
+            if (device_ns() - ts > kSpinLimitNs || (vload((const int *)&c->error) & ERR_SPIN)) {
+                atomicOr(&c->error, ERR_SPIN);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+}
+
+// One warp scans chunk ch of the per-brick minima for the bound (bd0, bd1).
+template <typename real>
+__device__ __forceinline__ void scan_chunk(const Geom &g, const DeviceState &s, int ch, real bd0,
+                                           real bd1, int lane)
+{
+    Control *c = s.ctrl;
+    const real *bmin = (const real *)s.bmin;
+    const real INF = inf_v<real>();
+    const unsigned long long cap = (unsigned long long)g.nbricks;
+    real l0 = INF, l1 = INF;
+    const long long first = (long long)ch * kScanChunk;
+    for (int j = 0; j < kScanChunk / 32; ++j) {
+        const long long b = first + 32 * j + lane;
+        bool sel = false;
+        if (b < g.nbricks) {
+            const real m0 = __ldcg(bmin + 2 * b), m1 = __ldcg(bmin + 2 * b + 1);
+            l0 = vmin(l0, m0);
+            l1 = vmin(l1, m1);
+            sel = (lt(m0, INF) && !lt(bd0, m0)) || (lt(m1, INF) && !lt(bd1, m1));
+        }
+        queue_push_warp(c, s.queue, cap, s.queued, b, sel, lane);
+    }
+    l0 = warp_min(l0);
+    l1 = warp_min(l1);
+    if (lane == 0) {
+        atomicMin(&c->scan_min[0], (unsigned long long)__double_as_longlong((double)l0));
+        atomicMin(&c->scan_min[1], (unsigned long long)__double_as_longlong((double)l1));
+        __threadfence();
+        atomicAdd(&c->scan_done, 1);
+    }
+}
+
+// Raise the bound (lane 0).  Returns true when this warp raised it.  For each
+// side, with m the smallest BAND minimum the last scan saw, the new bound is
+// max(bound, m) + stride, but while bricks are queued or marching at most
+// max_lead strides above floor(m / stride) * stride, so a small front
+// cannot run ahead, and a side whose scan saw no BAND cell waits (its next
+// BAND cells may be in flight in bricks notified but not yet marched).  With
+// nothing queued or marching every BAND value is above the bound, so the
+// bound always rises.
+__device__ bool try_raise(Control *c, const SolveParams &p, int nchunks, int pend)
+{
+    const int e = vload(&c->epoch);
+    if ((e & 1) || vload(&c->scan_done) < nchunks)
+        return false;
+    const double b0 = vloadd(&c->bound[0]), b1 = vloadd(&c->bound[1]);
+    if (b0 >= p.width && b1 >= p.width)
+        return false;
+    double nb[2];
+    const double bo[2] = {b0, b1};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        const double sm = __longlong_as_double((long long)vloadu(&c->scan_min[sd]));
+        double v;
+        if (!(sm < CUDART_INF)) {
+            v = pend == 0 ? p.width : bo[sd];
+        } else {
+            v = fmax(bo[sd], sm) + p.stride;
+            if (pend > 0 && p.stride < CUDART_INF)
+                v = fmin(v, (floor(sm / p.stride) + p.max_lead) * p.stride);
+            v = fmin(v, p.width);
+        }
+        nb[sd] = fmax(v, bo[sd]);
+    }
+    if (!(nb[0] > b0 || nb[1] > b1))
+        return false;
+    if (atomicCAS(&c->epoch, e, e + 1) != e)
+        return false;
+    if (p.max_restarts > 0 && (long long)vload(&c->restart) >= p.max_restarts) {
+        // the restart limit counts the raises too
+        atomicOr(&c->error, ERR_RESTARTS);
+        __threadfence();
+        atomicExch(&c->epoch, e + 2);
+        return false;
+    }
+    atomicExch(&c->scan_done, 0);
+    __threadfence();
+    *(volatile double *)&c->bound[0] = nb[0];
+    *(volatile double *)&c->bound[1] = nb[1];
+    atomicExch(&c->scan_min[0], 0x7ff0000000000000ull);
+    atomicExch(&c->scan_min[1], 0x7ff0000000000000ull);
+    atomicAdd(&c->restart, 1);
+    __threadfence();
+    atomicExch(&c->scan_next, 0);
+    __threadfence();
+    atomicExch(&c->epoch, e + 2);
+    return true;
+}
+
+// The solve is complete (lane 0; see above).
+__device__ bool solve_complete(Control *c, const SolveParams &p, int nchunks)
+{
+    const int e = vload(&c->epoch);
+    if ((e & 1) || vload(&c->scan_done) < nchunks)
+        return false;
+    __threadfence();
+    if (vload(&c->pending) != 0)
+        return false;
+    if (vloadd(&c->bound[0]) < p.width || vloadd(&c->bound[1]) < p.width)
+        return false;
+    __threadfence();
+    return vload(&c->epoch) == e;
+}
+
+// Lane 0: the next job of the warp.  job 0: march brick arg; 1: scan chunk
+// arg; 2: stop.  ticket is the queue ticket the warp holds (-1: none).
+__device__ void next_job(Control *c, unsigned long long *q, unsigned long long cap,
+                         const SolveParams &p, int nchunks, long long &ticket, int &job,
+                         long long &arg)
+{
+    if (ticket < 0)
+        ticket = (long long)atomicAdd(&c->q_head, 1ull);
+    unsigned long long *slot = q + ((unsigned long long)ticket % cap);
+    const unsigned long long want = (unsigned long long)ticket & 0xffffffffull;
+    unsigned long long t0 = device_ns();
+    unsigned long long seen_tail = vloadu(&c->q_tail);
+    int seen_done = vload(&c->scan_done), seen_epoch = vload(&c->epoch);
+    unsigned ns = 64;
+    for (;;) {
+        const unsigned long long v = vloadu(slot);
+        if (v != 0ull && (v >> 32) == want) {
+            atomicExch(slot, 0ull);
+            ticket = -1;
+            job = 0;
+            arg = (long long)(v & 0xffffffffull) - 1;
+            return;
+        }
+        if (vload(&c->error) & (ERR_SPIN | ERR_RESTARTS)) {
+            job = 2;
+            return;
+        }
+        if (vload(&c->scan_next) < nchunks) {
+            const int ch = atomicAdd(&c->scan_next, 1);
+            if (ch < nchunks) {
+                job = 1;
+                arg = ch;
+                return;
+            }
+        }
+        const int pend = vload(&c->pending);
+        if (pend < p.raise_at && try_raise(c, p, nchunks, pend))
+            continue;
+        if (pend == 0 && solve_complete(c, p, nchunks)) {
+            job = 2;
+            return;
+        }
+        const unsigned long long now = device_ns(), tail = vloadu(&c->q_tail);
+        const int dn = vload(&c->scan_done), ep = vload(&c->epoch);
+        if (tail != seen_tail || dn != seen_done || ep != seen_epoch) {
+            seen_tail = tail;
+            seen_done = dn;
+            seen_epoch = ep;
+            t0 = now;
+        } else if (now - t0 > kSpinLimitNs) {
+            break;
+        }
+        __nanosleep(ns);
+        if (ns < 2048)
+            ns <<= 1;
+    }
+    atomicOr(&c->error, ERR_SPIN);
+    job = 2;
+}
+
+template <typename real, bool kHetero>
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
+    k_march_continuous(Geom g, DeviceState s, SolveParams p, double spd_const_term)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    Control *ctrl = s.ctrl;
+    if (ctrl->done)
+        return;
+    const unsigned long long cap = (unsigned long long)g.nbricks;
+    const int nchunks = (int)((g.nbricks + kScanChunk - 1) / kScanChunk);
+    const real *bmin = (const real *)s.bmin;
+    unsigned long long *q = s.queue;
+    MarchStats st = {0, 0, 0, 0, 0};
+    long long ticket = -1;
+    for (;;) {
+        int job = 2;
+        long long arg = 0;
+        if (lane == 0)
+            next_job(ctrl, q, cap, p, nchunks, ticket, job, arg);
+        job = __shfl_sync(FULL, job, 0);
+        arg = __shfl_sync(FULL, arg, 0);
+        if (job == 2)
+            break;
+        if (job == 1) {
+            real bd0 = 0, bd1 = 0;
+            if (lane == 0) {
+                bd0 = (real)vloadd(&ctrl->bound[0]);
+                bd1 = (real)vloadd(&ctrl->bound[1]);
+            }
+            bd0 = __shfl_sync(FULL, bd0, 0);
+            bd1 = __shfl_sync(FULL, bd1, 0);
+            scan_chunk<real>(g, s, (int)arg, bd0, bd1, lane);
+            continue;
+        }
+        const long long b = arg;
+        unsigned long long mine = 0;
+        if (lane < kFaces)
+            mine = atomicExch(&s.fresh[b * kFaces + lane], 0ull);
+        real bound0 = 0, bound1 = 0;
+        if (lane == 0) {
+            bound0 = (real)vloadd(&ctrl->bound[0]);
+            bound1 = (real)vloadd(&ctrl->bound[1]);
+        }
+        __threadfence();
+        bound0 = __shfl_sync(FULL, bound0, 0);
+        bound1 = __shfl_sync(FULL, bound1, 0);
+        unsigned long long F[kFaces];
+#pragma unroll
+        for (int f = 0; f < kFaces; ++f)
+            F[f] = __shfl_sync(FULL, mine, f);
+        unsigned long long m;
+        long long nb;
+        march_brick<real, kHetero, 1, true>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+                                            lane, m, nb, st);
+        __threadfence();
+        __syncwarp();
+        if (m) {
+            atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
+            st.exchanges += (unsigned long long)__popcll(m);
+            __threadfence();
+            if (atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
+                atomicAdd(&ctrl->pending, 1);
+                queue_push(ctrl, q, cap, nb);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const real INF = inf_v<real>();
+            const real m0 = bmin[2 * b], m1 = bmin[2 * b + 1];
+            // end of the march: let others queue the brick again, and do it
+            // here if changes arrived meanwhile or the bound has risen above
+            // one of its BAND minima
+            atomicExch(&s.queued[b], 0u);
+            __threadfence();
+            bool again = false;
+#pragma unroll
+            for (int f = 0; f < kFaces; ++f)
+                again = again || (vload(&s.fresh[b * kFaces + f]) != 0ull);
+            const real nb0 = (real)vloadd(&ctrl->bound[0]), nb1 = (real)vloadd(&ctrl->bound[1]);
+            again = again || (lt(m0, INF) && !lt(nb0, m0)) || (lt(m1, INF) && !lt(nb1, m1));
+            if (again && atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
+                atomicAdd(&ctrl->pending, 1);
+                queue_push(ctrl, q, cap, b);
+            }
+            __threadfence();
+            atomicAdd(&ctrl->pending, -1);
+        }
+        __syncwarp();
+    }
+    flush_stats(ctrl, st, lane);
+}
+
 // Seed the queue of a restart: bricks with a BAND cell at or below the bound.
 template <typename real>
 __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, unsigned *queued,
@@ -1039,6 +1353,16 @@ __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, uns
 {
     if (ctrl->done)
         return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // no scan in progress (the continuous schedule raises the bound later)
+        const int nchunks = (int)((g.nbricks + kScanChunk - 1) / kScanChunk);
+        ctrl->epoch = 0;
+        ctrl->scan_next = nchunks;
+        ctrl->scan_done = nchunks;
+        // as if a scan had seen the bound itself: the first raise adds one stride
+        ctrl->scan_min[0] = (unsigned long long)__double_as_longlong(ctrl->bound[0]);
+        ctrl->scan_min[1] = (unsigned long long)__double_as_longlong(ctrl->bound[1]);
+    }
     const double bd0 = ctrl->bound[0], bd1 = ctrl->bound[1];
     const int lane = threadIdx.x & 31;
     for (long long b0 = blockIdx.x * (long long)blockDim.x; b0 < g.nbricks;
@@ -1119,6 +1443,7 @@ __global__ void k_control(Control *c, double width, double stride, long long max
     double mv0 = fmin(__longlong_as_double((long long)c->minbits[0]), width);
     double mv1 = fmin(__longlong_as_double((long long)c->minbits[1]), width);
     c->restart += 1;
+    c->host_restart += 1;
     if (mv0 >= width && mv1 >= width && c->dirty_count == 0u) {
         c->done = 1;
     } else if (max_restarts > 0 && c->restart > max_restarts) {
@@ -1207,6 +1532,8 @@ __global__ void k_reset_control(Control *c)
     c->done = 0;
     c->error = 0;
     c->restart = 0;
+    c->host_restart = 0;
+    c->epoch = 0;
 }
 
 // Brick layout -> the caller's x-fastest arrays (signed psi, public tags).
@@ -1371,16 +1698,22 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
-    if (p.schedule == kSchedulePersistent) {
+    if (one_launch_schedule(p.schedule)) {
         k_seed<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.ctrl, s.queued, s.queue);
         if (trace)
             k_trace_seed<<<1, 1, 0, st>>>(s.ctrl, trace);
         if (ev)
             cudaEventRecord(ev[0], st);
-        if (het)
+        if (p.schedule == kScheduleContinuous) {
+            if (het)
+                k_march_continuous<real, true><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+            else
+                k_march_continuous<real, false><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        } else if (het) {
             k_march_persistent<real, true><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
-        else
+        } else {
             k_march_persistent<real, false><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        }
         if (ev)
             cudaEventRecord(ev[1], st);
         return cudaGetLastError();
@@ -1429,6 +1762,8 @@ int configure_march()
     cudaFuncSetAttribute(k_march<real, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_march_persistent<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_march_persistent<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march_continuous<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_march_continuous<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1>, kMarchWarps * 32, sm);
     return n > 0 ? n : 1;

@@ -166,11 +166,15 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
-    p.schedule = cfg->schedule == kSchedulePhased ? kSchedulePhased : kSchedulePersistent;
+    p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
+                 : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
+                                                        : kScheduleContinuous;
     if (p.passes > 64)
         return error(FMM_ERR_INVALID, "exchange_passes must be at most 64");
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.raise_at = raise_threshold(s.march_ctas);
     if (cfg->dtype == FMM_F64) {
         p.spd_term = cfg->h * cfg->h;   // (h/F)^2 with F = 1
     } else {

@@ -30,13 +30,14 @@ def test_cache_roundtrip(tmp_path):
     autotune.save_cache(cache, path)
     got = autotune.params_for("reinit", "torch.float32", 1000, path=path)
     assert got == {"stride": math.inf, "bucket": 4.0, "exchange_passes": 2, "ctas": 0}
+    assert set(got) <= set(autotune.PARAMS)
     assert autotune.params_for("reinit", "float64", 1000, path=path) == {}
 
 
 def test_candidate_list():
     got = list(autotune.candidates(autotune.QUICK))
     assert got == [dict(c) for c in autotune.QUICK]
-    assert {c["schedule"] for c in got} == {1, 2}
+    assert {c["schedule"] for c in got} == {2, 3}
     assert all(set(c) <= set(autotune.PARAMS) for c in got)
 
 
@@ -53,9 +54,10 @@ def test_tune_small_problem_on_gpu(oracle, tmp_path):
     from parity_util import compare
     p = wl.random_spheres(shape=(40, 40, 40), count=4, seed=21)
     path = str(tmp_path / "tune.json")
-    search = {"stride": [4.0, 16.0, math.inf], "bucket": [1.0, 4.0], "exchange_passes": [1, 2]}
+    search = {"schedule": [1, 2], "stride": [4.0, 16.0, math.inf], "bucket": [1.0, 4.0],
+              "exchange_passes": [1, 2]}
     best, ms, table = autotune.tune(p, torch.float64, search=search, reps=1, path=path)
-    assert best is not None and ms > 0 and len(table) == 12
+    assert best is not None and ms > 0 and len(table) == 24
     assert autotune.params_for("reinit", torch.float64, p.n_points, path=path) == best
     phi = torch.as_tensor(p.phi0, dtype=torch.float64, device="cuda")
     with fmm.Solver(p.shape, p.h, dtype=torch.float64, **best) as s:

@@ -104,7 +104,7 @@ def test_fourier_speed(fmm, oracle, n, dt):
     compare(T, G, ref, dt)
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_fourier_speed_many_seeds(fmm, oracle, schedule):
     """Twelve seeds, each solved twice: brick marches run concurrently, so the
     order in which halo values and their change flags reach a brick differs
@@ -154,7 +154,7 @@ def test_reinit_single_sphere_64(fmm, oracle):
 
 @pytest.mark.parametrize("stride", [0.5, 1.0, 2.0, 3.5, math.inf])
 @pytest.mark.parametrize("bucket", [1.0, math.inf])
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_stride_bucket_schedule_do_not_change_the_result(fmm, oracle, stride, bucket, schedule):
     p = wl.random_spheres(shape=(40, 40, 40), count=5, seed=11)
     T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", stride=stride, bucket=bucket,
@@ -171,11 +171,22 @@ def test_phased_schedule_heterogeneous(fmm, oracle, dt):
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
-def test_narrow_band_width(fmm, oracle, dt):
+@pytest.mark.parametrize("schedule", [0, 1, 3])
+def test_narrow_band_width(fmm, oracle, dt, schedule):
     p = wl.random_spheres(shape=(36, 36, 36), count=4, seed=5)
     width = 0.08
-    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, dt, width=width)
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, dt, width=width, schedule=schedule)
     compare(T, G, ref, dt, width=width)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_continuous_schedule_shapes(fmm, oracle, dt):
+    for shape in [(16, 16, 16), (33, 17, 9), (1, 5, 1), (9, 9, 9)]:
+        rng = np.random.default_rng(sum(shape))
+        src = wl.random_cells(rng, shape, min(3, int(np.prod(shape))))
+        T, G, ref, _ = run_sources(fmm, oracle, shape, wl.spacing(shape), src, 1.7, dt,
+                                   schedule=3, stride=2.0)
+        compare(T, G, ref, dt)
 
 
 @pytest.mark.parametrize("schedule", [1, 2])
@@ -230,3 +241,22 @@ def test_restart_limit_reports_timeout(fmm):
         with pytest.raises(fmm.FmmError) as e:
             s.solve()
         assert e.value.code == fmm.FMM_ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3])
+def test_kernel_timing_and_trace(fmm, oracle, schedule):
+    """time_kernels: march time, one trace entry per march launch that did
+    work, and the same result as without timing."""
+    p = wl.random_spheres(shape=(48, 40, 44), count=5, seed=8)
+    phi = _dev(p.phi0, "f64")
+    for rep in range(2):                      # the event pool is reused
+        with fmm.Solver(p.shape, p.h, dtype=torch.float64, schedule=schedule, stride=4.0,
+                        time_kernels=True) as s:
+            T, G = s.reinit(phi)
+            st = s.stats()
+            tr = s.trace()
+        assert st["march_ms"] > 0.0 and st["march_launches"] >= 1
+        assert len(tr) == st["march_launches"]
+        assert all(ms >= 0.0 for _, _, _, ms in tr) and sum(b for _, _, b, _ in tr) > 0
+        assert st["restarts"] >= 2 and st["error_flags"] == 0
+    compare(_host(T), _host(G), oracle.solve_reinit(p.phi0, p.h), "f64")

@@ -108,7 +108,7 @@ typedef struct {
     int64_t march_launches;  /* launches of the brick-march kernel               */
     double march_ms;         /* summed device time of those launches (only with
                                 time_kernels; else 0)                          */
-    int64_t adjoint_iterations; /* select + march passes of the last fmm_adjoint */
+    int64_t adjoint_iterations; /* brick passes of the last fmm_adjoint          */
     int32_t error_flags;     /* device-side error bits (0 = none)                */
     int32_t reserved0;
     int64_t cell_solves;     /* Algorithm 11 evaluations in the brick marches    */

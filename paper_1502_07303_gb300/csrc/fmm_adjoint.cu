@@ -13,14 +13,18 @@
 // GPU formulation (pull, no atomics on values): every cell publishes
 // mu_p = lambda_p / D_p once it is done, with NaN meaning "not yet".  A cell
 // is ready when all its downwind neighbours have published; then
-// lambda_p = g_p + sum_q mu_q (T_q - T_p).  One warp processes one 8^3 brick
-// in rounds (the cells that became ready in a round are computed together);
-// downwind neighbours in other bricks are read from their published mu.  A
-// brick that finished boundary cells marks the bricks holding their upwind
-// neighbours dirty, and the dirty bricks run again (the select kernel of the
-// forward path builds the list) until no brick is dirty.  The order of the
-// sums is fixed, so the result is deterministic.
+// lambda_p = g_p + sum_q mu_q (T_q - T_p).  One persistent launch takes
+// bricks from the device-side queue of the forward path; a warp processes a
+// brick in rounds over its cells that are not done yet (per-lane 16-bit
+// masks; the cells that become ready in one step of a round are computed
+// together); downwind neighbours in other bricks are read from their
+// published mu.  A brick that finished boundary cells flags and queues the
+// bricks holding their upwind neighbours; a brick that ends its pass while a
+// flag arrived queues itself again.  The launch ends when no brick is queued
+// or being processed.  The order of the sums is fixed, so the result is
+// deterministic.
 #include "fmm_internal.h"
+#include "fmm_queue.cuh"
 
 #include <cmath>
 
@@ -76,41 +80,103 @@ __device__ __forceinline__ int tile_of(int c)
     return 111 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
 }
 
+// Tile index of the cell k (0..15) of lane (lx, lr): x = lx, y = lr + 4 (k & 1), z = k / 2.
+__device__ __forceinline__ int tb_of(int lx, int lr, int k)
+{
+    return 111 + lx + kTile * (lr + 4 * (k & 1)) + kTile * kTile * (k >> 1);
+}
+
 // Tape code of axis a of cell tp: 0 none, 1 minus neighbour, 2 plus.
 __device__ __forceinline__ int tape_axis(uint8_t tp, int a) { return (tp >> (2 * a)) & 3; }
 
 template <typename real>
 __device__ __forceinline__ bool is_nan(real v) { return v != v; }
 
-template <typename real, bool kHetero, int kMode>
+// a / b and sqrt(v) for the adjoint: single precision seeds refined by Newton
+// steps in double (relative error about 1e-15, far below the adjoint's
+// tolerance), which keeps most of the work off GB300's small FP64 pipe.
+// Operands outside the float range take the correctly rounded operation.
+__device__ __forceinline__ float adj_div(float a, float b) { return a / b; }
+__device__ __forceinline__ double adj_div(double a, double b)
+{
+    const float bf = (float)b;
+    if (!(fabsf(bf) >= 1e-30f && fabsf(bf) <= 1e30f))
+        return a / b;
+    double r = (double)(1.0f / bf);
+    r = r * fma(-b, r, 2.0);
+    r = r * fma(-b, r, 2.0);
+    const double q = a * r;
+    return fma(r, fma(-q, b, a), q);
+}
+__device__ __forceinline__ float adj_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double adj_sqrt(double v)
+{
+    const float vf = (float)v;
+    if (!(vf >= 1e-30f && vf <= 1e30f))
+        return sqrt(v);
+    const double r = (double)rsqrtf(vf);
+    const double y = v * r;
+    return fma(0.5 * r, fma(-y, y, v), y);
+}
+
+// Seed: every brick is queued once.
+__global__ void k_adj_seed(Geom g, Control *ctrl, unsigned *queued, unsigned long long *q)
+{
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < g.nbricks;
+         b += (long long)gridDim.x * blockDim.x) {
+        queued[b] = 1u;
+        q[b] = ((unsigned long long)(b & 0xffffffffll) << 32) | (unsigned long long)(b + 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->q_tail = (unsigned long long)g.nbricks;
+        ctrl->pending = (int)g.nbricks;
+    }
+}
+
+template <typename real, bool kHetero>
 __global__ void __launch_bounds__(kAdjWarps * 32)
-    k_adj_march(Geom g, DeviceState s, const real *__restrict__ dLdT, real *dlds, real *mu_g,
-                double h, double spd_const_term, int which)
+    k_adj_persistent(Geom g, DeviceState s, const real *__restrict__ dLdT, real *dlds, real *mu_g,
+                     double h, double spd_const_term)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     AdjTile<real> &W = reinterpret_cast<AdjTile<real> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
-    const long long n = (kMode == 0) ? g.nbricks : (long long)ctrl->n_list[which];
-    const int *work_list = which ? s.list[1] : s.list[0];
     const real *T = (const real *)s.T;
     const real *spd = (const real *)s.spd;
+    const unsigned long long cap = (unsigned long long)g.nbricks;
     const int off[3] = {1, kTile, kTile * kTile};
-    for (long long it = (long long)blockIdx.x * kAdjWarps + warp; it < n;
-         it += (long long)gridDim.x * kAdjWarps) {
-        const long long b = (kMode == 0) ? it : (long long)work_list[it];
+    const int lx = lane & 7, lr = (lane >> 3) & 3;
+    const real sh2_const = (real)(sqrt(spd_const_term) * h);
+    unsigned long long rounds_total = 0, passes = 0;
+    for (;;) {
+        long long b = -1;
+        if (lane == 0) {
+            b = queue_pop(ctrl, s.queue, cap);
+            if (b >= 0)
+                atomicExch(&s.dirty[b], 0u);   // the flags this pass answers
+            __threadfence();
+        }
+        b = __shfl_sync(FULL, b, 0);
+        if (b < 0)
+            break;
         int bx, by, bz;
         brick_xyz(g, b, bx, by, bz);
         const long long base = b * kB3;
-        // ---- stage T, mu, tape of the brick ------------------------------
+        // ---- stage T, mu, tape of the brick; cells still to do -------------
+        unsigned todo = 0;
 #pragma unroll 4
         for (int k = 0; k < 16; ++k) {
             const int c = lane + 32 * k;
             const int ti = tile_of(c);
+            const uint8_t tg = s.tag[base + c];
+            const real m = __ldcg(mu_g + base + c);
             W.T[ti] = T[base + c];
-            W.mu[ti] = mu_g[base + c];
-            W.tp[ti] = s.tape[base + c];
-            W.tg[c] = s.tag[base + c];
+            W.mu[ti] = m;
+            // cells that were not accepted have no upwind set
+            W.tp[ti] = accepted(tg) ? s.tape[base + c] : (uint8_t)0;
+            W.tg[c] = tg;
+            todo |= (unsigned)(accepted(tg) && is_nan(m)) << k;
         }
         // ---- halo: the face layers of the six neighbours ------------------
 #pragma unroll
@@ -131,10 +197,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                 const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
                 const long long ci = nb * kB3 + cx + kB * cy + kB * kB * cz;
                 tv = T[ci];
-                tpv = s.tape[ci];
                 mv = __ldcg(mu_g + ci);
-                if (!accepted(s.tag[ci]))
-                    tpv = 0;   // only accepted cells have upwind sets
+                tpv = accepted(s.tag[ci]) ? s.tape[ci] : (uint8_t)0;
             }
             const int hedge = dir < 0 ? 0 : kTile - 1;
             const int hx = axis == 0 ? hedge : u + 1;
@@ -146,35 +210,32 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             W.tp[hti] = tpv;
         }
         __syncwarp();
-        // interior cells that are not accepted have no upwind set either
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            const int c = lane + 32 * k;
-            if (!accepted(W.tg[c]))
-                W.tp[tile_of(c)] = 0;
-        }
-        __syncwarp();
 
-        // ---- rounds: cells whose downwind neighbours have all published ---
+        // ---- rounds over the cells still to do ------------------------------
         unsigned face_done = 0;   // bit f: a done cell has an upwind cell across face f
-        for (int round = 0; round < 4096; ++round) {
-            int progressed = 0;
-#pragma unroll 2
-            for (int k = 0; k < 16; ++k) {
-                const int c = lane + 32 * k;
-                const int ti = tile_of(c);
-                const real mup = W.mu[ti];
+        unsigned done_any = 0;
+        for (;;) {
+            const int steps = (int)__reduce_max_sync(FULL, (unsigned)__popc(todo));
+            if (steps == 0)
+                break;
+            unsigned rest = todo, done_now = 0;
+            for (int j = 0; j < steps; ++j) {
+                int k = -1;
+                if (rest) {
+                    k = __ffs(rest) - 1;
+                    rest &= rest - 1u;
+                }
                 bool ready = false;
                 real lam = (real)0, dsum = (real)0;
-                if (is_nan(mup)) {
+                int ti = 0;
+                if (k >= 0) {
+                    ti = tb_of(lx, lr, k);
                     ready = true;
                     const real Tp = W.T[ti];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        // neighbours on axis a: q = p - e_a (its upwind code 2
-                        // points at p) and q = p + e_a (code 1 points at p);
-                        // halo entries of missing bricks and cells that were
-                        // not accepted carry tape 0
+                        // downwind neighbours on axis a: q = p - e_a (its
+                        // upwind code 2 points at p) and q = p + e_a (code 1)
                         const int qm = ti - off[a], qp = ti + off[a];
                         if (tape_axis(W.tp[qm], a) == 2) {
                             const real m = W.mu[qm];
@@ -195,17 +256,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                             dsum += Tp - W.T[code == 1 ? qm : qp];
                     }
                 }
-                // the 32 cells of this step read before any of them publishes
+                // the cells of this step read before any of them publishes
                 __syncwarp();
                 if (ready) {
-                    const int cx = c & 7, cy = (c >> 3) & 7, cz = c >> 6;
-                    const int i = bx * kB + cx, j = by * kB + cy, kk = bz * kB + cz;
-                    const long long nat = ((long long)kk * g.ny + j) * g.nx + i;
+                    const int c = lane + 32 * k;
+                    const int cx = lx, cy = lr + 4 * (k & 1), cz = k >> 1;
+                    const int i = bx * kB + cx, jj = by * kB + cy, kk = bz * kB + cz;
+                    const long long nat = ((long long)kk * g.ny + jj) * g.nx + i;
                     lam += dLdT[nat];
-                    const real m = dsum > (real)0 ? lam / dsum : (real)0;
+                    const real m = dsum > (real)0 ? adj_div(lam, dsum) : (real)0;
                     W.mu[ti] = m;
-                    const real q = kHetero ? spd[base + c] : (real)spd_const_term;
-                    const real sh2 = sqrt(q) * (real)h;   // s_p h^2 with q = (h/F)^2
+                    // s_p h^2 = sqrt(q) h with q = (h/F)^2
+                    const real sh2 = kHetero ? adj_sqrt(spd[base + c]) * (real)h : sh2_const;
                     dlds[nat] = m * sh2;
                     const uint8_t tpc = W.tp[ti];
                     if (cx == 0 && tape_axis(tpc, 0) == 1) face_done |= 1u;
@@ -214,29 +276,56 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                     if (cy == 7 && tape_axis(tpc, 1) == 2) face_done |= 8u;
                     if (cz == 0 && tape_axis(tpc, 2) == 1) face_done |= 16u;
                     if (cz == 7 && tape_axis(tpc, 2) == 2) face_done |= 32u;
-                    progressed = 1;
+                    done_now |= 1u << k;
                 }
                 __syncwarp();
             }
-            if (!__any_sync(FULL, progressed))
+            todo &= ~done_now;
+            done_any |= done_now;
+            ++rounds_total;
+            if (!__any_sync(FULL, done_now != 0u))
                 break;
         }
         // ---- publish mu, wake the bricks that hold upwind neighbours ------
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            const int c = lane + 32 * k;
-            mu_g[base + c] = W.mu[tile_of(c)];
+        for (unsigned mm = done_any; mm; mm &= mm - 1u) {
+            const int k = __ffs(mm) - 1;
+            mu_g[base + lane + 32 * k] = W.mu[tb_of(lx, lr, k)];
         }
+        __threadfence();
         face_done = __reduce_or_sync(FULL, face_done);
         if (lane < kFaces && ((face_done >> lane) & 1u)) {
             const int f = lane, axis = f >> 1, dir = (f & 1) ? 1 : -1;
             const int nbx = bx + (axis == 0 ? dir : 0);
             const int nby = by + (axis == 1 ? dir : 0);
             const int nbz = bz + (axis == 2 ? dir : 0);
-            if (nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 && nbz < g.nbz)
-                s.dirty[((long long)nbz * g.nby + nby) * g.nbx + nbx] = 1u;
+            if (nbx >= 0 && nbx < g.nbx && nby >= 0 && nby < g.nby && nbz >= 0 && nbz < g.nbz) {
+                const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
+                atomicExch(&s.dirty[nb], 1u);
+                __threadfence();
+                if (atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
+                    atomicAdd(&ctrl->pending, 1);
+                    queue_push(ctrl, s.queue, cap, nb);
+                }
+            }
         }
         __syncwarp();
+        if (lane == 0) {
+            // end of the pass: queue the brick again if a flag arrived meanwhile
+            atomicExch(&s.queued[b], 0u);
+            __threadfence();
+            if (vload((const int *)&s.dirty[b]) != 0 && atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
+                atomicAdd(&ctrl->pending, 1);
+                queue_push(ctrl, s.queue, cap, b);
+            }
+            __threadfence();
+            atomicAdd(&ctrl->pending, -1);
+            ++passes;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && passes) {
+        atomicAdd(&ctrl->marches, passes);
+        atomicAdd(&ctrl->rounds, rounds_total);
     }
 }
 
@@ -257,27 +346,27 @@ template <typename real>
 size_t adj_smem() { return sizeof(AdjTile<real>) * kAdjWarps; }
 
 template <typename real>
-cudaError_t adj_launch(const Geom &g, const DeviceState &s, const AdjointArgs &a, int mode,
-                       int which, cudaStream_t st)
+cudaError_t adj_persistent_launch(const Geom &g, const DeviceState &s, const AdjointArgs &a,
+                                  cudaStream_t st)
 {
     const size_t sm = adj_smem<real>();
-    const int ctas = s.march_ctas;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool het = s.spd != nullptr;
-    if (mode == 0) {
-        if (het)
-            k_adj_march<real, true, 0><<<ctas, kAdjWarps * 32, sm, st>>>(
-                g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, which);
-        else
-            k_adj_march<real, false, 0><<<ctas, kAdjWarps * 32, sm, st>>>(
-                g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, which);
-    } else {
-        if (het)
-            k_adj_march<real, true, 1><<<ctas, kAdjWarps * 32, sm, st>>>(
-                g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, which);
-        else
-            k_adj_march<real, false, 1><<<ctas, kAdjWarps * 32, sm, st>>>(
-                g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, which);
-    }
+    if (het)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<real, true>,
+                                                      kAdjWarps * 32, sm);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<real, false>,
+                                                      kAdjWarps * 32, sm);
+    const int ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (het)
+        k_adj_persistent<real, true><<<ctas, kAdjWarps * 32, sm, st>>>(
+            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term);
+    else
+        k_adj_persistent<real, false><<<ctas, kAdjWarps * 32, sm, st>>>(
+            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term);
     return cudaGetLastError();
 }
 
@@ -285,10 +374,8 @@ template <typename real>
 void adj_configure()
 {
     const int sm = (int)adj_smem<real>();
-    cudaFuncSetAttribute(k_adj_march<real, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_march<real, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_march<real, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_march<real, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_adj_persistent<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_adj_persistent<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 int grid_cap(long long n, int threads, int cap)
@@ -315,11 +402,13 @@ cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_march(int dtype, const Geom &g, const DeviceState &s,
-                                 const AdjointArgs &a, int mode, int which, cudaStream_t st)
+cudaError_t launch_adjoint_persistent(int dtype, const Geom &g, const DeviceState &s,
+                                      const AdjointArgs &a, cudaStream_t st)
 {
-    return dtype == 1 ? adj_launch<double>(g, s, a, mode, which, st)
-                      : adj_launch<float>(g, s, a, mode, which, st);
+    const int nb = grid_cap(g.nbricks, 256, 152 * 32);
+    k_adj_seed<<<nb, 256, 0, st>>>(g, s.ctrl, s.queued, s.queue);
+    return dtype == 1 ? adj_persistent_launch<double>(g, s, a, st)
+                      : adj_persistent_launch<float>(g, s, a, st);
 }
 
 cudaError_t launch_adjoint_pending(int dtype, const Geom &g, const AdjointArgs &a, unsigned *count,

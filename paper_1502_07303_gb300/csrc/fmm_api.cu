@@ -475,37 +475,20 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     a.h = hd->params.h;
     a.spd_term = hd->params.spd_term;
     // every cell becomes ready once its downwind neighbours have published;
-    // bricks run again while a neighbour finished cells they depend on
+    // one persistent launch processes bricks until none is queued
     FMM_CUDA(hd, launch_reset_control(s, st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
-    FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
-    FMM_CUDA(hd, launch_adjoint_march(dt, g, s, a, 0, 1, st));
-    const auto t0 = std::chrono::steady_clock::now();
-    const double limit_s = hd->cfg.timeout_s > 0 ? (double)hd->cfg.timeout_s : 600.0;
-    long long batch = 1, iters = 0;
-    for (;;) {
-        for (long long r = 0; r < batch; ++r) {
-            FMM_CUDA(hd, launch_reset_list(s, 1, st));
-            FMM_CUDA(hd, launch_select(dt, g, s, 1, st));
-            FMM_CUDA(hd, launch_adjoint_march(dt, g, s, a, 1, 1, st));
-        }
-        iters += batch;
-        FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
-        FMM_CUDA(hd, cudaStreamSynchronize(st));
-        if (hd->h_ctrl->n_list[1] == 0)
-            break;
-        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s)
-            return fail(hd, FMM_ERR_TIMEOUT, "the adjoint exceeded its wall-clock limit (timeout_s)");
-        if (batch < 16)
-            batch *= 2;
-    }
+    FMM_CUDA(hd, launch_adjoint_persistent(dt, g, s, a, st));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
     FMM_CUDA(hd, cudaMemsetAsync(hd->adj_count, 0, sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_pending(dt, g, a, hd->adj_count, st));
     unsigned left = 0;
     FMM_CUDA(hd, cudaMemcpyAsync(&left, hd->adj_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     FMM_CUDA(hd, cudaStreamSynchronize(st));
-    hd->stats.adjoint_iterations = iters;
+    hd->stats.adjoint_iterations = (int64_t)hd->h_ctrl->marches;
+    if (hd->h_ctrl->error & ERR_SPIN)
+        return fail(hd, FMM_ERR_TIMEOUT, "adjoint: a device wait exceeded its time limit");
     if (left != 0)
         return fail(hd, FMM_ERR_STATE, "adjoint: some accepted cells could not be ordered");
     return FMM_OK;

@@ -70,7 +70,8 @@ struct Control {
     alignas(128) int epoch;
     int scan_next;
     int scan_done;
-    int pad3[2];
+    int scan_clean;                  // the last scan started with nothing in flight
+    int pad3;
     unsigned long long scan_min[2];
     int pad4[22];
 };
@@ -205,9 +206,8 @@ struct AdjointArgs {
 cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
                                 const AdjointArgs &a, cudaStream_t stream);
 // mode 0: every brick; mode 1: the bricks of work list `which`
-cudaError_t launch_adjoint_march(int dtype, const Geom &g, const DeviceState &s,
-                                 const AdjointArgs &a, int mode, int which,
-                                 cudaStream_t stream);
+cudaError_t launch_adjoint_persistent(int dtype, const Geom &g, const DeviceState &s,
+                                      const AdjointArgs &a, cudaStream_t st);
 cudaError_t launch_adjoint_pending(int dtype, const Geom &g, const AdjointArgs &a,
                                    unsigned *count, cudaStream_t stream);
 

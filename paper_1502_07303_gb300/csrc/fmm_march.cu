@@ -32,6 +32,7 @@
 // return an upper bound; the owner then flags the change and the brick is
 // marched again before termination can be declared.
 #include "fmm_internal.h"
+#include "fmm_queue.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -886,86 +887,6 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // past the limit the kernel sets ERR_SPIN and returns.
 // ---------------------------------------------------------------------------
 
-// Waits give up after kSpinLimitNs nanoseconds of device time.
-constexpr unsigned long long kSpinLimitNs = 4000000000ull;
-
-__device__ __forceinline__ unsigned long long device_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
-{
-    return *(const volatile unsigned long long *)p;
-}
-__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
-
-// Push brick b (the caller has claimed queued[b] and counted it in pending).
-__device__ __forceinline__ bool queue_push(Control *c, unsigned long long *q, unsigned long long cap,
-                                           long long b)
-{
-    const unsigned long long t = atomicAdd(&c->q_tail, 1ull);
-    const unsigned long long v = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
-    unsigned long long *slot = q + (t % cap);
-    const unsigned long long t0 = device_ns();
-    for (;;) {
-        if (atomicCAS(slot, 0ull, v) == 0ull)
-            return true;
-        if (device_ns() - t0 > kSpinLimitNs || (vload((const int *)&c->error) & ERR_SPIN))
-            break;
-        __nanosleep(32);
-    }
-    atomicOr(&c->error, ERR_SPIN);
-    return false;
-}
-
-// Pop a brick: -1 when the restart is complete (or on a timeout).  Each
-// caller takes a ticket from q_head and waits on its own slot, so idle warps
-// poll distinct lines with a growing back-off instead of racing on the head.
-// pending == 0 means that no push is in flight or to come, so a ticket whose
-// slot is still empty then ends the caller's loop.  The time limit counts from
-// the last push seen anywhere.
-__device__ __forceinline__ long long queue_pop(Control *c, unsigned long long *q,
-                                               unsigned long long cap)
-{
-    const unsigned long long h = atomicAdd(&c->q_head, 1ull);
-    unsigned long long *slot = q + (h % cap);
-    const unsigned long long want = h & 0xffffffffull;
-    unsigned long long t0 = device_ns(), seen = vload(&c->q_tail);
-    unsigned ns = 64;
-    for (;;) {
-        unsigned long long v = vload(slot);
-        if (v != 0ull && (v >> 32) == want) {
-            atomicExch(slot, 0ull);
-            return (long long)(v & 0xffffffffull) - 1;
-        }
-        if (vload(&c->pending) == 0) {
-            v = vload(slot);
-            if (v != 0ull && (v >> 32) == want) {
-                atomicExch(slot, 0ull);
-                return (long long)(v & 0xffffffffull) - 1;
-            }
-            return -1;
-        }
-        if (vload(&c->error) & ERR_SPIN)
-            return -1;
-        const unsigned long long now = device_ns(), tail = vload(&c->q_tail);
-        if (tail != seen) {
-            seen = tail;
-            t0 = now;
-        } else if (now - t0 > kSpinLimitNs) {
-            break;
-        }
-        __nanosleep(ns);
-        if (ns < 2048)
-            ns <<= 1;
-    }
-    atomicOr(&c->error, ERR_SPIN);
-    return -1;
-}
-
 template <typename real, bool kHetero>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
@@ -1124,10 +1045,13 @@ __device__ __forceinline__ void scan_chunk(const Geom &g, const DeviceState &s, 
 // side, with m the smallest BAND minimum the last scan saw, the new bound is
 // max(bound, m) + stride, but while bricks are queued or marching at most
 // max_lead strides above floor(m / stride) * stride, so a small front
-// cannot run ahead, and a side whose scan saw no BAND cell waits (its next
-// BAND cells may be in flight in bricks notified but not yet marched).  With
-// nothing queued or marching every BAND value is above the bound, so the
-// bound always rises.
+// cannot run ahead.  A scan that saw no BAND cell on a side proves the side
+// finished only if it started with nothing queued or marching (a clean
+// scan): otherwise the side's next BAND cells may have been in flight, in
+// bricks notified but not yet marched, and the side waits while bricks are
+// in flight, or rises by one stride (which starts a clean scan) when none
+// are.  With nothing queued or marching every BAND value is above the
+// bound, so the bound always rises.
 __device__ bool try_raise(Control *c, const SolveParams &p, int nchunks, int pend)
 {
     const int e = vload(&c->epoch);
@@ -1143,7 +1067,12 @@ __device__ bool try_raise(Control *c, const SolveParams &p, int nchunks, int pen
         const double sm = __longlong_as_double((long long)vloadu(&c->scan_min[sd]));
         double v;
         if (!(sm < CUDART_INF)) {
-            v = pend == 0 ? p.width : bo[sd];
+            if (pend > 0)
+                v = bo[sd];
+            else if (vload(&c->scan_clean))
+                v = p.width;
+            else
+                v = fmin(bo[sd] + p.stride, p.width);
         } else {
             v = fmax(bo[sd], sm) + p.stride;
             if (pend > 0 && p.stride < CUDART_INF)
@@ -1164,6 +1093,7 @@ __device__ bool try_raise(Control *c, const SolveParams &p, int nchunks, int pen
         return false;
     }
     atomicExch(&c->scan_done, 0);
+    atomicExch(&c->scan_clean, pend == 0 ? 1 : 0);
     __threadfence();
     *(volatile double *)&c->bound[0] = nb[0];
     *(volatile double *)&c->bound[1] = nb[1];
@@ -1359,6 +1289,7 @@ __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, uns
         ctrl->epoch = 0;
         ctrl->scan_next = nchunks;
         ctrl->scan_done = nchunks;
+        ctrl->scan_clean = 0;
         // as if a scan had seen the bound itself: the first raise adds one stride
         ctrl->scan_min[0] = (unsigned long long)__double_as_longlong(ctrl->bound[0]);
         ctrl->scan_min[1] = (unsigned long long)__double_as_longlong(ctrl->bound[1]);

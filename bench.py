@@ -53,21 +53,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel):
-    """DRAM bytes per finalised point of the march kernel from the committed
-    ncu summary, valid only for that kernel while its source is unchanged."""
+def traffic_record(kernel, dtype):
+    """DRAM bytes per finalised point of a march kernel and dtype from the
+    committed ncu summary (lines "kernel dtype source_sha256_16 bytes"), valid
+    only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "k_march_traffic.txt")
     src = os.path.join(ROOT, "paper_1502_07303_gb300", "csrc", "fmm_march.cu")
     try:
-        rec = {}
-        for line in open(path):
-            if ":" in line and not line.startswith("#"):
-                k, v = line.split(":", 1)
-                rec[k.strip()] = v.strip()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") != sha or rec.get("kernel") != kernel:
-            return None
-        return float(rec["dram_bytes_per_point"])
+        for line in open(path):
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#") and f[0] == kernel and f[1] == dtype \
+                    and f[2] == sha:
+                return float(f[3])
+        return None
     except Exception:
         return None
 
@@ -393,6 +392,16 @@ def run_gpu(args):
     if sampler:
         sampler.start()
     t_wall = time.perf_counter()
+    if args.part == "f64":
+        r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream,
+                      tuned["f64"])
+        if sampler:
+            sampler.stop()
+        if rank == 0:
+            print(json.dumps({"part": "f64", "ms_per_step": r64["ms"], "params": tuned["f64"],
+                              "march_ms": r64["march_ms"], "march_launches": r64["march_launches"],
+                              "stats": r64["stats"]}), flush=True)
+        return 0
     r32 = measure(fmm, torch, phi32, p, torch.float32, args.steps, args.warmup, flush, stream,
                   tuned["f32"])
     torch.cuda.synchronize()
@@ -437,7 +446,7 @@ def run_gpu(args):
         avg_launch_s = r["march_ms"] / launches / 1e3
         alg_per_launch = ALG_BYTES[dt] * pts / launches
         achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-        bpp = traffic_record(kernel) if dt == "f32" else None
+        bpp = traffic_record(kernel, dt)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": (bpp * pts / launches) if bpp else None,
                 "kernel": kernel, "peak_kind": peak_kind,
@@ -493,8 +502,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID, help=argparse.SUPPRESS)
-    ap.add_argument("--part", default="all", choices=["all", "f32"],
-                    help="f32: only the fp32 timed solves (for profiling)")
+    ap.add_argument("--part", default="all", choices=["all", "f32", "f64"],
+                    help="f32 / f64: only the timed solves of one dtype (for profiling)")
     ap.add_argument("--params", type=_params, default=None,
                     help="restart parameters as JSON (skips the autotuner), e.g. "
                          "'{\"schedule\": 2, \"stride\": \"inf\"}'")

@@ -10,6 +10,8 @@ times (library defaults).
   sign of every cell, and the first-order distance error bound (the oracle's
   own error grows from 0.8 h at 32^3 to 1.5 h at 192^3).
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -87,15 +89,30 @@ def sampled_local_solves(oracle, T, G, h, F, n=3000, seed=0):
     return worst
 
 
-@pytest.mark.parametrize("dt", ["f64", "f32"])
-def test_bench_workload_256_full_compare(fmm, oracle, dt):
+# the library defaults, and the configurations the bench's autotuner picks
+# for this workload (persistent without restarts; continuous at 2 h without a
+# lead limit)
+BENCH_PARAMS = [{}, {"schedule": 2, "stride": math.inf},
+                {"schedule": 3, "stride": 2.0, "max_lead": 1 << 20}]
+
+
+@pytest.fixture(scope="module")
+def c2():
     p = wl.random_spheres(n=256, count=32, seed=2)
+    return p, {}
+
+
+@pytest.mark.parametrize("params", BENCH_PARAMS, ids=["defaults", "persistent-inf", "continuous-2h"])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_bench_workload_256_full_compare(fmm, oracle, c2, dt, params):
+    p, refs = c2
     phi = torch.as_tensor(p.phi0, dtype=DT[dt], device="cuda")
-    with fmm.Solver(p.shape, p.h, dtype=DT[dt]) as s:
+    with fmm.Solver(p.shape, p.h, dtype=DT[dt], **params) as s:
         T, G = s.reinit(phi)
-    phi_q = np.asarray(p.phi0, np.float32).astype(np.float64) if dt == "f32" else p.phi0
-    ref = oracle.solve_reinit(phi_q, p.h)
-    compare(T.cpu().numpy(), G.cpu().numpy(), ref, dt)
+    if dt not in refs:
+        phi_q = np.asarray(p.phi0, np.float32).astype(np.float64) if dt == "f32" else p.phi0
+        refs[dt] = oracle.solve_reinit(phi_q, p.h)
+    compare(T.cpu().numpy(), G.cpu().numpy(), refs[dt], dt)
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])

@@ -93,6 +93,14 @@ typedef struct {
                               strides of the smallest BAND value the last scan
                               saw (a small front cannot run ahead); 0 -> 3;
                               large values remove the limit                   */
+    int32_t wait_limit_ms; /* every device-side wait (brick queue, bound
+                              raise) gives up after this long without any
+                              progress, sets an error bit and the call returns
+                              FMM_ERR_TIMEOUT; 0 -> 4000                      */
+    int32_t hold_queue;    /* testing only: 1 counts one phantom brick as
+                              queued, so the persistent and continuous
+                              schedules' waits run into wait_limit_ms (the
+                              error path without a fault); 0 normally       */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */

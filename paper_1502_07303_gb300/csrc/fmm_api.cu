@@ -128,7 +128,7 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
         s.spd = nullptr;
     }
     hd->speed_const = speed ? 1.0 : speed_const;
-    FMM_CUDA(hd, launch_reset_control(s, hd->stream));
+    FMM_CUDA(hd, launch_reset_control(s, hd->stream, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, launch_load_speed(hd->cfg.dtype, hd->geom, s, hd->params.h, speed,
                                    hd->speed_const, hd->stream));
     FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost,
@@ -158,7 +158,7 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     const Geom &g = hd->geom;
     const int dt = hd->cfg.dtype;
     cudaStream_t st = hd->stream;
-    FMM_CUDA(hd, launch_reset_control(s, st));
+    FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
@@ -212,7 +212,7 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
         }
         FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
         FMM_CUDA(hd, cudaStreamSynchronize(st));
-        if (hd->h_ctrl->done)
+        if (hd->h_ctrl->done || (hd->h_ctrl->error & (ERR_SPIN | ERR_ROUNDS | ERR_RESTARTS)))
             break;
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > limit_s) {
@@ -356,6 +356,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
+    p.hold = cfg->hold_queue != 0;
 
     auto bail = [&](fmm_status code) {
         g_create_error = hd->err;
@@ -476,7 +478,7 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     a.spd_term = hd->params.spd_term;
     // every cell becomes ready once its downwind neighbours have published;
     // one persistent launch processes bricks until none is queued
-    FMM_CUDA(hd, launch_reset_control(s, st));
+    FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
     FMM_CUDA(hd, launch_adjoint_persistent(dt, g, s, a, st));
@@ -581,6 +583,8 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
+    p.hold = cfg->hold_queue != 0;
     p.spd_term = 0.0;
     auto bail = [&](fmm_status code) {
         g_create_error = hd->err;

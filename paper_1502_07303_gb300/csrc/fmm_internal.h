@@ -73,7 +73,9 @@ struct Control {
     int scan_clean;                  // the last scan started with nothing in flight
     int pad3;
     unsigned long long scan_min[2];
-    int pad4[22];
+    unsigned long long wait_ns;      // limit of every device wait without progress
+    int hold;                        // testing: one brick counted as pending forever
+    int pad4[19];
 };
 
 struct Geom {
@@ -97,6 +99,8 @@ struct SolveParams {
     int raise_at;       // continuous schedule: raise the bound when fewer
                         // bricks than this are queued or marching
     double max_lead;    // continuous schedule: lead of the bound in strides
+    unsigned long long wait_ns;   // limit of a device wait without progress
+    int hold;           // testing: keep one phantom brick pending
 };
 
 constexpr int kSchedulePhased = 1;
@@ -181,7 +185,8 @@ inline int marches_per_restart(int passes, int schedule)
 cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s,
                            const SolveParams &p, cudaStream_t stream, cudaEvent_t *ev,
                            int *trace);
-cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream);
+cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream,
+                                 unsigned long long wait_ns, int hold);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);
 int march_blocks_per_sm(int dtype);

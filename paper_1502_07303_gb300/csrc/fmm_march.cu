@@ -970,7 +970,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // works as a sequence lock: odd while a raise rewrites the bound and the scan
 // counters.  The solve is complete when no raise is in progress, the last
 // scan is done, nothing is queued or marching and the bound has reached width
-// on both sides.  Every wait is bounded (kSpinLimitNs without any progress).
+// on both sides.  Every wait is bounded (wait_ns without any progress).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double vloadd(const double *p) { return *(const volatile double *)p; }
@@ -998,9 +998,9 @@ __device__ __forceinline__ void queue_push_warp(Control *c, unsigned long long *
         const unsigned long long t = t0 + __popc(ball & ((1u << lane) - 1u));
         const unsigned long long v = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
         unsigned long long *slot = q + (t % cap);
-        const unsigned long long ts = device_ns();
+        const unsigned long long ts = device_ns(), lim = vload(&c->wait_ns);
         while (atomicCAS(slot, 0ull, v) != 0ull) {
-            if (device_ns() - ts > kSpinLimitNs || (vload((const int *)&c->error) & ERR_SPIN)) {
+            if (device_ns() - ts > lim || (vload((const int *)&c->error) & ERR_SPIN)) {
                 atomicOr(&c->error, ERR_SPIN);
                 break;
             }
@@ -1134,6 +1134,7 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
     const unsigned long long want = (unsigned long long)ticket & 0xffffffffull;
     unsigned long long t0 = device_ns();
     unsigned long long seen_tail = vloadu(&c->q_tail);
+    const unsigned long long lim = vloadu(&c->wait_ns);
     int seen_done = vload(&c->scan_done), seen_epoch = vload(&c->epoch);
     unsigned ns = 64;
     for (;;) {
@@ -1171,7 +1172,7 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
             seen_done = dn;
             seen_epoch = ep;
             t0 = now;
-        } else if (now - t0 > kSpinLimitNs) {
+        } else if (now - t0 > lim) {
             break;
         }
         __nanosleep(ns);
@@ -1290,6 +1291,8 @@ __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, uns
         ctrl->scan_next = nchunks;
         ctrl->scan_done = nchunks;
         ctrl->scan_clean = 0;
+        if (ctrl->hold)
+            atomicAdd(&ctrl->pending, 1);   // testing: the queue never drains
         // as if a scan had seen the bound itself: the first raise adds one stride
         ctrl->scan_min[0] = (unsigned long long)__double_as_longlong(ctrl->bound[0]);
         ctrl->scan_min[1] = (unsigned long long)__double_as_longlong(ctrl->bound[1]);
@@ -1370,6 +1373,10 @@ __global__ void k_control(Control *c, double width, double stride, long long max
 {
     if (c->done)
         return;
+    if (c->error & (ERR_SPIN | ERR_ROUNDS | ERR_RESTARTS)) {
+        c->done = 1;   // a device error ends the solve (reported by the host)
+        return;
+    }
     const unsigned long long INF_BITS = 0x7ff0000000000000ull;
     double mv0 = fmin(__longlong_as_double((long long)c->minbits[0]), width);
     double mv1 = fmin(__longlong_as_double((long long)c->minbits[1]), width);
@@ -1448,8 +1455,10 @@ __global__ void k_select(Geom g, const real *__restrict__ bmin, unsigned *dirty,
     }
 }
 
-__global__ void k_reset_control(Control *c)
+__global__ void k_reset_control(Control *c, unsigned long long wait_ns, int hold)
 {
+    c->wait_ns = wait_ns;
+    c->hold = hold;
     const unsigned long long INF_BITS = 0x7ff0000000000000ull;
     c->minbits[0] = INF_BITS;
     c->minbits[1] = INF_BITS;
@@ -1761,9 +1770,10 @@ cudaError_t launch_restart(int dtype, const Geom &g, const DeviceState &s, const
                       : restart_impl<float>(g, s, p, st, ev, trace);
 }
 
-cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st)
+cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st, unsigned long long wait_ns,
+                                 int hold)
 {
-    k_reset_control<<<1, 1, 0, st>>>(s.ctrl);
+    k_reset_control<<<1, 1, 0, st>>>(s.ctrl, wait_ns, hold);
     return cudaGetLastError();
 }
 

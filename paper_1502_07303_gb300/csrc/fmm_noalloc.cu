@@ -174,6 +174,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
+    p.hold = cfg->hold_queue != 0;
     p.raise_at = raise_threshold(s.march_ctas);
     if (cfg->dtype == FMM_F64) {
         p.spd_term = cfg->h * cfg->h;   // (h/F)^2 with F = 1
@@ -191,7 +193,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
             return cuda_error(e_, #call);               \
     } while (0)
     // clear what the solve reads before it writes
-    NA_CUDA(launch_reset_control(s, st));
+    NA_CUDA(launch_reset_control(s, st, p.wait_ns, p.hold));
     NA_CUDA(cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     NA_CUDA(cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     NA_CUDA(cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));

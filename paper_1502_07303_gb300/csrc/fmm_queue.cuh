@@ -2,17 +2,15 @@
 // the adjoint: a ring of (sequence << 32 | brick + 1) words, its head, tail
 // and pending counters in the control block, and a time source for bounded
 // waits.  A brick is in the ring at most once (its queued flag), so a ring of
-// one slot per brick never overflows.  Every wait gives up after kSpinLimitNs
-// of device time without progress: it sets ERR_SPIN and returns.
+// one slot per brick never overflows.  Every wait gives up after wait_ns of
+// the control block (device time without progress): it sets ERR_SPIN and
+// returns.
 #pragma once
 
 #include "fmm_internal.h"
 
 namespace fmmgb {
 namespace {
-
-// Waits give up after kSpinLimitNs nanoseconds of device time.
-constexpr unsigned long long kSpinLimitNs = 4000000000ull;
 
 __device__ __forceinline__ unsigned long long device_ns()
 {
@@ -34,11 +32,11 @@ __device__ __forceinline__ bool queue_push(Control *c, unsigned long long *q, un
     const unsigned long long t = atomicAdd(&c->q_tail, 1ull);
     const unsigned long long v = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
     unsigned long long *slot = q + (t % cap);
-    const unsigned long long t0 = device_ns();
+    const unsigned long long t0 = device_ns(), lim = vload(&c->wait_ns);
     for (;;) {
         if (atomicCAS(slot, 0ull, v) == 0ull)
             return true;
-        if (device_ns() - t0 > kSpinLimitNs || (vload((const int *)&c->error) & ERR_SPIN))
+        if (device_ns() - t0 > lim || (vload((const int *)&c->error) & ERR_SPIN))
             break;
         __nanosleep(32);
     }
@@ -59,6 +57,7 @@ __device__ __forceinline__ long long queue_pop(Control *c, unsigned long long *q
     unsigned long long *slot = q + (h % cap);
     const unsigned long long want = h & 0xffffffffull;
     unsigned long long t0 = device_ns(), seen = vload(&c->q_tail);
+    const unsigned long long lim = vload(&c->wait_ns);
     unsigned ns = 64;
     for (;;) {
         unsigned long long v = vload(slot);
@@ -80,7 +79,7 @@ __device__ __forceinline__ long long queue_pop(Control *c, unsigned long long *q
         if (tail != seen) {
             seen = tail;
             t0 = now;
-        } else if (now - t0 > kSpinLimitNs) {
+        } else if (now - t0 > lim) {
             break;
         }
         __nanosleep(ns);

@@ -33,7 +33,8 @@ class FmmConfig(ctypes.Structure):
                 ("ctas", ctypes.c_int32), ("timeout_s", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p),
                 ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32),
+                ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
@@ -135,7 +136,7 @@ class Solver:
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
                  max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
-                 schedule=0, max_lead=0, stream=None):
+                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, stream=None):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
@@ -156,6 +157,8 @@ class Solver:
         cfg.exchange_passes = int(exchange_passes)
         cfg.schedule = int(schedule)
         cfg.max_lead = int(min(max_lead, 1 << 30))
+        cfg.wait_limit_ms = int(wait_limit_ms)
+        cfg.hold_queue = int(hold_queue)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)
@@ -272,7 +275,7 @@ class Batch:
 
     def __init__(self, shapes, hs, dtype=torch.float32, width=math.inf, stride=0.0, bucket=0.0,
                  exchange_passes=0, ctas=0, max_restarts=0, timeout_s=0, time_kernels=False,
-                 schedule=0, max_lead=0, stream=None):
+                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, stream=None):
         self.lib = load()
         self.code, self.dtype = _dtype_code(dtype)
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
@@ -293,6 +296,8 @@ class Batch:
         cfg.time_kernels = 1 if time_kernels else 0
         cfg.schedule = int(schedule)
         cfg.max_lead = int(min(max_lead, 1 << 30))
+        cfg.wait_limit_ms = int(wait_limit_ms)
+        cfg.hold_queue = int(hold_queue)
         cfg.stream = _stream_handle(stream)
         handle = ctypes.c_void_p()
         rc = self.lib.fmm_create_batch(n, dims.ctypes.data, hh.ctypes.data, ctypes.byref(cfg),

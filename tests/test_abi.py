@@ -60,3 +60,26 @@ def test_create_error_without_gpu_is_reported():
     assert b"outside" in lib.fmm_last_error(None)
     assert lib.fmm_solve(None, None, None) == fmm.FMM_ERR_INVALID
     lib.fmm_destroy(None)
+
+
+def _struct_fields(name):
+    """Field names of the C struct typedef `name` in include/fmm.h, in order."""
+    text = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    bodies = dict((n, b) for b, n in re.findall(r"typedef struct \{([^{}]*)\}\s*(\w+);", text))
+    body = bodies[name]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        for part in decl.split(","):   # int64_t nx, ny, nz
+            ids = re.findall(r"[A-Za-z_][A-Za-z_0-9]*", part)
+            if ids:
+                fields.append(ids[-1])
+    return fields
+
+
+def test_binding_structs_match_header():
+    """The ctypes structs carry the header's fields in the header's order."""
+    from paper_1502_07303_gb300 import fmm
+    for cname, pyst in (("fmm_config", fmm.FmmConfig), ("fmm_stats", fmm.FmmStats),
+                        ("fmm_trace_entry", fmm.FmmTraceEntry)):
+        assert [f[0] for f in pyst._fields_] == _struct_fields(cname), cname

@@ -5,6 +5,7 @@ Sizes span several 8^3 bricks and ragged tails; the oracle finishes each case
 in seconds.  Tolerances: max |dT| <= 1e-12 max|T| (fp64), 2e-5 max|T| (fp32),
 with identical tags (identical accepted sets)."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -260,3 +261,21 @@ def test_kernel_timing_and_trace(fmm, oracle, schedule):
         assert all(ms >= 0.0 for _, _, _, ms in tr) and sum(b for _, _, b, _ in tr) > 0
         assert st["restarts"] >= 2 and st["error_flags"] == 0
     compare(_host(T), _host(G), oracle.solve_reinit(p.phi0, p.h), "f64")
+
+
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_device_wait_limit_reports_timeout_and_recovers(fmm, oracle, schedule):
+    """A device wait that runs out (the brick queue held open by one phantom
+    pending brick) sets an error bit, the call returns FMM_ERR_TIMEOUT after
+    about wait_limit_ms, and the GPU and the library stay usable."""
+    p = wl.random_spheres(shape=(32, 32, 32), count=3, seed=4)
+    phi = _dev(p.phi0, "f64")
+    t0 = time.perf_counter()
+    with fmm.Solver(p.shape, p.h, dtype=torch.float64, schedule=schedule, wait_limit_ms=50,
+                    hold_queue=1) as s:
+        with pytest.raises(fmm.FmmError) as e:
+            s.reinit(phi)
+        assert e.value.code == fmm.FMM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60
+    T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", schedule=schedule)
+    compare(T, G, ref, "f64")

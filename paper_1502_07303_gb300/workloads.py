@@ -254,14 +254,19 @@ def batch_shapes(n_grids=256, lo=32, hi=192, seed=4):
 
 def batch(n_grids=256, lo=32, hi=192, seed=4, device=None):
     """Independent reinitialisation problems of uneven sizes: per grid 1-8
-    random spheres with the modulated level set, h = 1 / max extent."""
+    random spheres with the modulated level set, h = 1 / max extent.  The
+    sphere law of the 32-sphere workload is applied to each grid's own box
+    (extents e = (nx, ny, nz) h): centres uniform in [0.15, 0.85] e per
+    axis, radii uniform in [0.05, 0.15] min(e), so every grid has a front."""
     dims, counts, rng = batch_shapes(n_grids, lo, hi, seed)
     out = []
     for g in range(n_grids):
         nx, ny, nz = (int(v) for v in dims[g])
         shape = (nz, ny, nx)
-        sph = draw_spheres(rng, int(counts[g]))
         h = spacing(shape)
+        ext = np.array([nx, ny, nz], dtype=np.float64) * h
+        unit = draw_spheres(rng, int(counts[g]))
+        sph = Spheres(unit.centres * ext[None, :], unit.radii * float(ext.min()))
         out.append(Problem(f"batch{g}", shape, h,
                            phi0=spheres_phi0(shape, sph, h=h, device=device),
                            meta={"spheres": sph}))

@@ -130,3 +130,36 @@ def test_eikonal_autograd_function(fmm, oracle):
     d = s0.grad.cpu().numpy()
     assert np.max(np.abs(d - d_ref)) <= 1e-11 * np.max(np.abs(d_ref))
     solver.close()
+
+
+def test_adjoint_finite_differences_512_fp64(fmm):
+    """The bench's adjoint workload in full (512^3, Fourier speed, 8 sources,
+    64 receivers, fp64, library defaults): dL/ds from fmm_adjoint against
+    central differences of L(s) along two smooth random directions, each
+    from two GPU forward solves (a property that holds at any size)."""
+    p = wl.fourier_sources(n=512, n_sources=8, n_receivers=64, seed=3, device="cuda")
+    F = p.speed.to(torch.float64).contiguous()
+    rec = torch.as_tensor(np.asarray(p.receivers), device="cuda")
+    g = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+    g[rec[:, 2], rec[:, 1], rec[:, 0]] = 1.0
+    with fmm.Solver(p.shape, p.h, dtype=torch.float64, speed=F, sources=p.sources,
+                    record_tape=True) as s:
+        s.solve(want_tags=False)
+        dLds = s.adjoint(g)
+    s0 = 1.0 / F
+
+    def L(slow):
+        with fmm.Solver(p.shape, p.h, dtype=torch.float64, speed=(1.0 / slow).contiguous(),
+                        sources=p.sources) as sv:
+            T, _ = sv.solve(want_tags=False)
+        return float(T[rec[:, 2], rec[:, 1], rec[:, 0]].sum())
+
+    n = p.shape[0]
+    x = (torch.arange(n, device="cuda", dtype=torch.float64) + 0.5) / n
+    for kx, ky, kz in ((1, 2, 3), (3, 1, 2)):
+        v = (torch.sin(2 * np.pi * kx * x)[None, None, :] * torch.cos(2 * np.pi * ky * x)[None, :, None]
+             * torch.sin(2 * np.pi * kz * x + 0.3)[:, None, None])
+        eps = 1e-6 * float(torch.linalg.vector_norm(s0)) / float(torch.linalg.vector_norm(v))
+        fd = (L(s0 + eps * v) - L(s0 - eps * v)) / (2 * eps)
+        ad = float((dLds * v).sum())
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)

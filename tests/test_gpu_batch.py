@@ -73,3 +73,29 @@ def test_batch_handle_rejects_single_grid_calls(fmm):
             s.solve()
         assert e.value.code == fmm.FMM_ERR_STATE
         s.handle = None
+
+
+def test_bench_batch_256_grids_sampled(fmm, oracle):
+    """The bench's batched workload in full (256 grids, axes in [32, 192],
+    fp32, one batch handle, library defaults): six of the smaller grids
+    element by element against the oracle; every grid whose phi0 changes sign
+    fully accepted, every other grid (its spheres lie outside a thin grid)
+    entirely FAR."""
+    probs = wl.batch(n_grids=256, lo=32, hi=192, seed=4, device="cuda")
+    phis = [p.phi0.to(torch.float32).contiguous() for p in probs]
+    with fmm.Batch([p.shape for p in probs], [p.h for p in probs], dtype=torch.float32) as b:
+        Ts, Gs = b.reinit(phis)
+        st = b.stats()
+    assert st["error_flags"] == 0
+    for p, phi, G in zip(probs, phis, Gs):
+        front = bool((phi > 0).any()) and bool((phi <= 0).any())
+        if front:
+            assert int((G == 0).sum()) == 0 and int((G == 1).sum()) == 0, p.name
+        else:
+            assert int((G != 0).sum()) == 0, p.name
+    order = sorted(range(len(probs)), key=lambda i: probs[i].n_points)
+    for i in order[:6]:
+        p = probs[i]
+        phi_q = p.phi0.to(torch.float32).to(torch.float64).cpu().numpy()
+        ref = oracle.solve_reinit(phi_q, p.h)
+        compare(Ts[i].cpu().numpy(), Gs[i].cpu().numpy(), ref, "f32")

@@ -9,7 +9,9 @@
  * of Algorithm 16: subdomains (here 8x8x8 bricks of the grid) march locally up
  * to a global bound that rises by a stride at every restart, exchange changed
  * overlap data, and a global reduction of the front minimum sets the next
- * bound and decides termination.
+ * bound and decides termination.  The restart loop runs on the GPU; by
+ * default (fmm_config.schedule) one launch runs the whole solve and the bound
+ * rises as soon as a restart runs out of parallel work.
  *
  * Conventions shared by every entry point
  *   - Grid arrays are nx*ny*nz elements, x fastest: idx = (k*ny + j)*nx + i,
@@ -45,7 +47,8 @@ typedef enum {
     FMM_ERR_INVALID = 1,   /* bad argument (sizes, pointers, speed <= 0, NaN) */
     FMM_ERR_OOM = 2,       /* device allocation failed                        */
     FMM_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
-    FMM_ERR_TIMEOUT = 4,   /* an iteration or restart limit was reached       */
+    FMM_ERR_TIMEOUT = 4,   /* a round, restart, device-wait (wait_limit_ms) or
+                              wall-clock (timeout_s) limit was reached         */
     FMM_ERR_STATE = 5      /* call order violated (e.g. adjoint before solve) */
 } fmm_status;
 

@@ -8,15 +8,20 @@
 //   Initialize_Heap_Parallel (Alg. 9)       -> k_march<mode 0> (one relax of
 //                                               every cell next to a FIX cell)
 //   local minima + AllReduce (Alg. 16)      -> k_reduce + k_control
-//   March_Narrow_Band_Parallel (Alg. 12)    -> k_march<mode 1> on a work list
+//   March_Narrow_Band_Parallel (Alg. 12)    -> march_brick, run by one of three
+//                                               restart schedules (below)
 //   Collect/Exchange/Integrate (Alg. 13-15) -> write-back to HBM plus per-face
-//                                               "fresh" bit masks and a dirty
-//                                               flag on the neighbour brick; the
-//                                               select kernel moves the masks to
-//                                               the neighbour's inbox and its next
+//                                               "fresh" bit masks on the
+//                                               neighbour brick, whose next
 //                                               staging reads the new values
-//   second march of Alg. 16                 -> k_march<mode 1> on the bricks
-//                                               made dirty by the first march
+//   second march of Alg. 16                 -> the neighbour is marched again
+//                                               (queued, or listed as dirty)
+//
+// Restart schedules: continuous (k_march_continuous: one launch for the whole
+// solve, bricks from a device-side queue, the bound raised in the kernel when
+// a restart runs out of parallel work), persistent (k_seed +
+// k_march_persistent: one queue-driven launch per restart) and phased
+// (k_select + k_march<mode 1>: one launch per pass over a work list).
 //
 // Inside a brick (one warp per brick) the heap of Algorithm 12 is replaced by
 // a bucketed, label-correcting march: each round accepts every BAND cell whose |psi| is

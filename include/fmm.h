@@ -44,7 +44,7 @@ extern "C" {
 
 typedef enum {
     FMM_OK = 0,
-    FMM_ERR_INVALID = 1,   /* bad argument (sizes, pointers, speed <= 0, NaN) */
+    FMM_ERR_INVALID = 1,   /* bad argument (sizes, pointers, speed < 0, NaN, inf) */
     FMM_ERR_OOM = 2,       /* device allocation failed                        */
     FMM_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
     FMM_ERR_TIMEOUT = 4,   /* a round, restart, device-wait (wait_limit_ms) or
@@ -130,8 +130,11 @@ typedef struct fmm_handle fmm_handle;
 /*
  * fmm_create -- allocate a solver for one grid and load its speed field.
  *   cfg          : host pointer, copied.
- *   speed        : device, nx*ny*nz values of F (dtype), all finite and > 0;
- *                  or NULL for the constant speed_const (> 0).
+ *   speed        : device, nx*ny*nz values of F (dtype), all finite and >= 0;
+ *                  F = 0 marks an obstacle cell (the obstacles of test case
+ *                  6, Sec. 5.1): it is never reached and stays FAR with
+ *                  psi = +inf, and no front passes through it; or NULL for
+ *                  the constant speed_const (> 0).
  *   src_ijk      : host, n_src (i, j, k) int64 triples: the point sources used
  *                  by fmm_solve (psi = 0, KNOWN_FIX; Algorithm 8); may be NULL
  *                  when n_src == 0.

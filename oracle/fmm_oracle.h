@@ -51,7 +51,9 @@ int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, double h,
 
 /* Algorithm 9 followed by Algorithm 12 with bound_band(+-1) = width (the
  * sequential reference of Sec. 5.2).  T and G come from an init call and are
- * updated in place.  speed == NULL means a constant speed speed_const.
+ * updated in place.  speed == NULL means a constant speed speed_const.  A
+ * cell with F = 0 is an obstacle (test case 6 of Sec. 5.1): its term
+ * F^-2 = +inf gives no finite root, so it stays FAR with psi = +inf.
  * Optional outputs (NULL to skip):
  *   order[n]   : cell indices in acceptance (heap pop) order; *n_order = count
  *   tape[n]    : for each cell, the upwind set of the root that gave its final

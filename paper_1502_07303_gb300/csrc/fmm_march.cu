@@ -125,8 +125,12 @@ __device__ __forceinline__ double vsqrt(double v)
     const double y = v * r;
     return fma(0.5 * r, fma(-y, y, v), y);
 }
-// Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance).
-__device__ __forceinline__ float vsqrt(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
+// Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance);
+// +inf (the speed term of an obstacle cell) stays +inf.
+__device__ __forceinline__ float vsqrt(float v)
+{
+    return v > 0.0f ? (v < CUDART_INF_F ? v * rsqrtf(v) : v) : 0.0f;
+}
 
 // The quadratic of Algorithm 11, sum_i (t - psi_i)^2 / h^2 = 1/F^2 over the
 // upwind set, is solved for the unknown shifted by the smallest upwind value
@@ -377,7 +381,9 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
             F = speed[((long long)k * g.ny + j) * g.nx + i];
         if (out)
             F = (real)1;
-        if (!(F > (real)0) || !(F < inf_v<real>()))
+        // F = 0: an obstacle cell, whose speed term (h/F)^2 is +inf, so no
+        // solve ever gives it a finite value
+        if (!(F >= (real)0) || !(F < inf_v<real>()))
             atomicOr(&ctrl->error, ERR_SPEED);
         if (spd)
             spd[b * kB3 + t] = speed_term(F, h);

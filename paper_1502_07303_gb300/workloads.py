@@ -145,7 +145,9 @@ def fourier_speed(shape, modes: FourierModes, h=None, device=None):
 
 def paper_speed(shape, case, h=None):
     """Speed functions of Sec. 5.1 on the [-0.5, 0.5]^3 cube of the paper
-    (Eq. (8)-(10)); case in {3, 4, 5}."""
+    (Eq. (8)-(10)); case in {3, 4, 5, 6}: case 6 is F = 1 with F = 0 inside
+    four concentric spherical shells of width 1/24 (radii 0.15, 0.25, 0.35,
+    0.45), each with a cylindrical gap around the z axis (Eq. (11))."""
     h = spacing(shape) if h is None else h
     x, y, z = _axes(shape, h)
     x, y, z = x - 0.5, y - 0.5, z - 0.5
@@ -155,6 +157,17 @@ def paper_speed(shape, case, h=None):
         return 1.0 + 0.5 * np.sin(20 * np.pi * x) * np.sin(20 * np.pi * y) * np.sin(20 * np.pi * z)
     if case == 5:
         return 1.0 - 0.99 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y) * np.sin(2 * np.pi * z)
+    if case == 6:
+        w = 1.0 / 24.0
+        R = np.sqrt(x * x + y * y + z * z)
+        r = np.sqrt(x * x + y * y)
+        wall = np.zeros(np.broadcast(x, y, z).shape, dtype=bool)
+        for r0, gap, below in ((0.15, 0.05, True), (0.25, 0.10, False), (0.35, 0.10, True),
+                               (0.45, 0.10, False)):
+            shell = (R > r0) & (R < r0 + w)
+            hole = (r < gap) & ((z < 0) if below else (z > 0))
+            wall |= shell & ~hole
+        return np.where(wall, 0.0, 1.0)
     raise ValueError(case)
 
 

@@ -279,3 +279,18 @@ def test_device_wait_limit_reports_timeout_and_recovers(fmm, oracle, schedule):
     assert time.perf_counter() - t0 < 60
     T, G, ref, _ = run_reinit(fmm, oracle, p.phi0, p.h, "f64", schedule=schedule)
     compare(T, G, ref, "f64")
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
+def test_paper_case6_obstacles(fmm, oracle, dt, schedule):
+    """Sec. 5.1 case 6: point source at the centre, four concentric spherical
+    shells of F = 0 with gaps (Eq. (11)); obstacle cells stay FAR."""
+    n = 48
+    shape = (n, n, n)
+    F = wl.paper_speed(shape, 6)
+    T, G, ref, _ = run_sources(fmm, oracle, shape, 1.0 / n, [(n // 2, n // 2, n // 2)], F, dt,
+                               schedule=schedule)
+    compare(T, G, ref, dt)
+    assert np.all(G[F == 0.0] == 0) and np.all(np.isinf(T[F == 0.0]))
+    assert np.all(G[F > 0.0] >= 2)   # every open cell is reached through the gaps

@@ -380,3 +380,53 @@ def test_adjoint_tangent_dot_product(oracle):
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
     # FIX cells get no gradient; a source's slowness cannot move T
     assert np.all(dLds[r["G"] == oracle.KNOWN_FIX] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# obstacles (F = 0, test case 6 of Sec. 5.1)
+# ---------------------------------------------------------------------------
+
+def test_full_wall_blocks_and_leaves_source_side_unchanged(oracle):
+    """A plane of F = 0 cells across the grid with the source on one side:
+    the source side is exactly the unobstructed solution (wall cells are never
+    known, and they lie downwind of every cell on that side), the wall and
+    everything behind it stay FAR with psi = +inf."""
+    shape = (14, 13, 20)
+    h = 1.0 / 20
+    src = [(4, 6, 7)]
+    F = np.ones(shape)
+    F[:, :, 11] = 0.0
+    free = oracle.solve_sources(shape, src, h)
+    wall = oracle.solve_sources(shape, src, h, speed=F)
+    assert np.array_equal(wall["T"][:, :, :11], free["T"][:, :, :11])
+    assert np.all(np.isinf(wall["T"][:, :, 11:]))
+    assert np.all(wall["G"][:, :, 11:] == oracle.FAR)
+
+
+def test_wall_with_gap_detours(oracle):
+    """A wall with a square gap: every value is at least the unobstructed one
+    (an obstacle only removes paths), cells behind the wall are reached
+    through the gap, the wall stays FAR, and fast sweeping agrees."""
+    shape = (16, 16, 24)
+    h = 1.0 / 24
+    src = [(3, 8, 8)]
+    F = np.ones(shape)
+    F[:, :, 10] = 0.0
+    F[6:10, 6:10, 10] = 1.0      # the gap
+    free = oracle.solve_sources(shape, src, h)
+    r = oracle.solve_sources(shape, src, h, speed=F)
+    T, G = r["T"], r["G"]
+    wall = F == 0.0
+    assert np.all(np.isinf(T[wall])) and np.all(G[wall] == oracle.FAR)
+    open_ = ~wall
+    assert np.all(np.isfinite(T[open_]))
+    assert np.all(T[open_] >= free["T"][open_] - 1e-15)
+    # the corner cell just behind the wall is reached around the wall's edge
+    # of the gap: its straight path crosses the wall far from the gap
+    assert T[0, 0, 11] > free["T"][0, 0, 11] + h
+    fixed = (G == oracle.KNOWN_FIX).astype(np.uint8)
+    A, rounds = oracle.fast_sweep(np.where(fixed == 1, np.abs(T), 0.0), fixed, h, speed=F)
+    assert rounds < 10000
+    fin = np.isfinite(T)
+    assert np.array_equal(np.isfinite(A), fin)
+    assert np.max(np.abs(A[fin] - T[fin])) <= 1e-13 * np.max(T[fin])

@@ -294,3 +294,20 @@ def test_paper_case6_obstacles(fmm, oracle, dt, schedule):
     compare(T, G, ref, dt)
     assert np.all(G[F == 0.0] == 0) and np.all(np.isinf(T[F == 0.0]))
     assert np.all(G[F > 0.0] >= 2)   # every open cell is reached through the gaps
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
+def test_paper_case2_plane(fmm, oracle, dt, schedule):
+    """Sec. 5.1 case 2: the plane 100x + y + 2z = 0 through the centre of the
+    [-0.5, 0.5]^3 cube, positive where 100x + y + 2z > 0; every cell depends
+    on three upwind cells of the same pattern, so information crosses each
+    x plane corner to corner in strict order."""
+    n = 40
+    shape = (n, n, n)
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h - 0.5
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    phi = (100 * x + y + 2 * z) / math.sqrt(100 ** 2 + 1 + 4)
+    T, G, ref, _ = run_reinit(fmm, oracle, phi, h, dt, schedule=schedule)
+    compare(T, G, ref, dt)

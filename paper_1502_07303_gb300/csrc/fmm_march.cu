@@ -42,6 +42,7 @@
 #include <cfloat>
 #include <cmath>
 #include <math_constants.h>
+#include <type_traits>
 
 namespace fmmgb {
 namespace {
@@ -112,18 +113,20 @@ __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ double vmin(double a, double b) { return lt(a, b) ? a : b; }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
-// Double square root: the single-precision reciprocal square root refined by
-// one Newton step in double (relative error about 1e-13, far below the
-// solver's tolerance; it keeps most of the work off the FP64 pipe).  Values
-// outside the float range take the library square root.
+// Double square root: single-precision estimates y of sqrt(v) and rh of
+// 1/(2 sqrt(v)) refined by one Newton step in double, y + rh (v - y^2)
+// (relative error about 1e-14, far below the solver's tolerance; two double
+// FMAs keep most of the work off the FP64 pipe).  Values outside the float
+// range take the library square root.
 __device__ __forceinline__ double vsqrt(double v)
 {
     const float vf = (float)v;
     if (!(vf >= 1e-30f && vf <= 1e30f))
         return sqrt(v);
-    const double r = (double)rsqrtf(vf);
-    const double y = v * r;
-    return fma(0.5 * r, fma(-y, y, v), y);
+    const float rf = rsqrtf(vf);
+    const double y = (double)(vf * rf);
+    const double rh = (double)(0.5f * rf);
+    return fma(rh, fma(-y, y, v), y);
 }
 // Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance);
 // +inf (the speed term of an obstacle cell) stays +inf.
@@ -504,10 +507,12 @@ struct MarchStats {
 // One brick march.  F_in: the halo cells whose known value changed since the
 // brick last ran (kMode 1); kMode 0 derives them from the known halo cells.
 // kFresh: read the brick and halo through L2 (the persistent kernel, where the
-// brick may have been written by another SM during the same launch).  On
+// brick may have been written by another SM during the same launch).  kTape:
+// record the upwind set of every solve for the adjoint (without it the
+// compiler drops the set bookkeeping of Algorithm 11 altogether).  On
 // return, lanes 0..5 hold in notify_m / notify_nb the changed boundary cells
 // and the neighbour brick across face = lane (mode 1).
-template <typename real, bool kHetero, int kMode, bool kFresh>
+template <typename real, bool kHetero, int kMode, bool kFresh, bool kTape>
 __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s, const SolveParams &p,
                                             double spd_const_term, WarpTile<real> &W, long long b,
                                             const unsigned long long *F_in, real bound0, real bound1,
@@ -539,7 +544,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         const uint8_t sv = t & ST_MASK;
         W.tv[c] = v;
         W.kv[tile_of(c)] = sv >= ST_KNOWN ? v : INF;
-        if (s.tape)
+        if (kTape)
             W.tp[c] = kFresh ? __ldcg(s.tape + base + c) : s.tape[base + c];
         band |= (unsigned)(sv == ST_BAND) << k;
         known |= (unsigned)(sv >= ST_KNOWN) << k;
@@ -650,7 +655,8 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             if (c >= 0 && lt(cand, tc)) {
                 W.tv[c] = cand;
                 W.kv[ti] = INF;
-                W.tp[c] = cset;
+                if (kTape)
+                    W.tp[c] = cset;
                 atomicOr(&W.improved[c & 31], 1u << (c >> 5));
             }
             __syncwarp();
@@ -766,7 +772,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             t |= TG_NEG;
         T[base + c] = v;
         tag[base + c] = t;
-        if (s.tape)
+        if (kTape)
             s.tape[base + c] = W.tp[c];
         if (kMode == 1 && ((chg >> k) & 1u)) {
             const int y = lr + 4 * (k & 1), z = k >> 1;
@@ -829,7 +835,7 @@ __device__ __forceinline__ void flush_stats(Control *ctrl, MarchStats &st, int l
 // Algorithm 12 over the bricks of work list `which` (taken one at a time from
 // a shared counter) with the change masks the select kernel moved to the
 // inbox; changes are flagged in the neighbours' live masks and dirty flags.
-template <typename real, bool kHetero, int kMode>
+template <typename real, bool kHetero, int kMode, bool kTape>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
 {
@@ -864,7 +870,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = kMode == 1 ? s.inbox[b * kFaces + f] : 0ull;
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, kMode, false>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, kMode, false, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                                  lane, m, nb, st);
         if (kMode == 1 && m) {
             atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
@@ -898,7 +904,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // past the limit the kernel sets ERR_SPIN and returns.
 // ---------------------------------------------------------------------------
 
-template <typename real, bool kHetero>
+template <typename real, bool kHetero, bool kTape>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
@@ -930,7 +936,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, 1, true>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, 1, true, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                             lane, m, nb, st);
         // publish the write-back before flagging anything
         __threadfence();
@@ -1194,7 +1200,7 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
     job = 2;
 }
 
-template <typename real, bool kHetero>
+template <typename real, bool kHetero, bool kTape>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_continuous(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
@@ -1248,7 +1254,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, 1, true>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, 1, true, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                             lane, m, nb, st);
         __threadfence();
         __syncwarp();
@@ -1639,12 +1645,31 @@ __global__ void k_reset_list(Control *c, int which)
     c->work[which] = 0u;
 }
 
+// Calls f with the speed-field and tape flags as compile-time constants
+// (std::true_type / std::false_type), one kernel instantiation per pair.
+template <typename Fn>
+void with_flags(bool het, bool tape, Fn &&f)
+{
+    using Y = std::true_type;
+    using N = std::false_type;
+    if (het) {
+        if (tape)
+            f(Y{}, Y{});
+        else
+            f(Y{}, N{});
+    } else if (tape) {
+        f(N{}, Y{});
+    } else {
+        f(N{}, N{});
+    }
+}
+
 template <typename real>
 cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams &p,
                          cudaStream_t st, cudaEvent_t *ev, int *trace)
 {
     const int rb = grid_for(g.nbricks, 256, 4096);
-    const bool het = s.spd != nullptr;
+    const bool het = s.spd != nullptr, tape = s.tape != nullptr;
     const double sct = p.spd_term;
     const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
@@ -1655,16 +1680,13 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             k_trace_seed<<<1, 1, 0, st>>>(s.ctrl, trace);
         if (ev)
             cudaEventRecord(ev[0], st);
-        if (p.schedule == kScheduleContinuous) {
-            if (het)
-                k_march_continuous<real, true><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        with_flags(het, tape, [&](auto H, auto P) {
+            constexpr bool h = decltype(H)::value, t = decltype(P)::value;
+            if (p.schedule == kScheduleContinuous)
+                k_march_continuous<real, h, t><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
             else
-                k_march_continuous<real, false><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
-        } else if (het) {
-            k_march_persistent<real, true><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
-        } else {
-            k_march_persistent<real, false><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
-        }
+                k_march_persistent<real, h, t><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+        });
         if (ev)
             cudaEventRecord(ev[1], st);
         return cudaGetLastError();
@@ -1679,10 +1701,10 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             k_trace<<<1, 1, 0, st>>>(s.ctrl, which, pass, trace + 3 * pass);
         if (ev)
             cudaEventRecord(ev[2 * pass], st);
-        if (het)
-            k_march<real, true, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
-        else
-            k_march<real, false, 1><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
+        with_flags(het, tape, [&](auto H, auto P) {
+            k_march<real, decltype(H)::value, 1, decltype(P)::value>
+                <<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
+        });
         if (ev)
             cudaEventRecord(ev[2 * pass + 1], st);
     }
@@ -1696,10 +1718,10 @@ cudaError_t front_init_impl(const Geom &g, const DeviceState &s, const SolvePara
     const long long need = (g.nbricks + kMarchWarps - 1) / kMarchWarps;
     const int nb = (int)(need < s.march_ctas ? need : s.march_ctas);
     const size_t sm = march_smem<real>();
-    if (s.spd)
-        k_march<real, true, 0><<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
-    else
-        k_march<real, false, 0><<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
+    with_flags(s.spd != nullptr, s.tape != nullptr, [&](auto H, auto P) {
+        k_march<real, decltype(H)::value, 0, decltype(P)::value>
+            <<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
+    });
     return cudaGetLastError();
 }
 
@@ -1707,16 +1729,18 @@ template <typename real>
 int configure_march()
 {
     const int sm = (int)march_smem<real>();
-    cudaFuncSetAttribute(k_march<real, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march<real, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march<real, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march<real, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march_persistent<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march_persistent<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march_continuous<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_march_continuous<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    for (int h = 0; h < 2; ++h)
+        for (int t = 0; t < 2; ++t)
+            with_flags(h != 0, t != 0, [&](auto H, auto P) {
+                constexpr bool hh = decltype(H)::value, tt = decltype(P)::value;
+                cudaFuncSetAttribute(k_march<real, hh, 1, tt>, attr, sm);
+                cudaFuncSetAttribute(k_march<real, hh, 0, tt>, attr, sm);
+                cudaFuncSetAttribute(k_march_persistent<real, hh, tt>, attr, sm);
+                cudaFuncSetAttribute(k_march_continuous<real, hh, tt>, attr, sm);
+            });
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1>, kMarchWarps * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1, true>, kMarchWarps * 32, sm);
     return n > 0 ? n : 1;
 }
 

@@ -25,6 +25,7 @@
 // deterministic.
 #include "fmm_internal.h"
 #include "fmm_queue.cuh"
+#include "fmm_fp64.cuh"
 
 #include <cmath>
 
@@ -92,32 +93,12 @@ __device__ __forceinline__ int tape_axis(uint8_t tp, int a) { return (tp >> (2 *
 template <typename real>
 __device__ __forceinline__ bool is_nan(real v) { return v != v; }
 
-// a / b and sqrt(v) for the adjoint: single precision seeds refined by Newton
-// steps in double (relative error about 1e-15, far below the adjoint's
-// tolerance), which keeps most of the work off GB300's small FP64 pipe.
-// Operands outside the float range take the correctly rounded operation.
+// a / b and sqrt(v) for the adjoint; in double, float seeds refined by
+// Newton steps without the FP64 pipe's slow conversions (fmm_fp64.cuh).
 __device__ __forceinline__ float adj_div(float a, float b) { return a / b; }
-__device__ __forceinline__ double adj_div(double a, double b)
-{
-    const float bf = (float)b;
-    if (!(fabsf(bf) >= 1e-30f && fabsf(bf) <= 1e30f))
-        return a / b;
-    double r = (double)(1.0f / bf);
-    r = r * fma(-b, r, 2.0);
-    r = r * fma(-b, r, 2.0);
-    const double q = a * r;
-    return fma(r, fma(-q, b, a), q);
-}
+__device__ __forceinline__ double adj_div(double a, double b) { return div_fp64(a, b); }
 __device__ __forceinline__ float adj_sqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double adj_sqrt(double v)
-{
-    const float vf = (float)v;
-    if (!(vf >= 1e-30f && vf <= 1e30f))
-        return sqrt(v);
-    const double r = (double)rsqrtf(vf);
-    const double y = v * r;
-    return fma(0.5 * r, fma(-y, y, v), y);
-}
+__device__ __forceinline__ double adj_sqrt(double v) { return sqrt_fp64(v); }
 
 // Seed: every brick is queued once.
 __global__ void k_adj_seed(Geom g, Control *ctrl, unsigned *queued, unsigned long long *q)

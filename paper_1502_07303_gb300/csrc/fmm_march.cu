@@ -38,6 +38,7 @@
 // marched again before termination can be declared.
 #include "fmm_internal.h"
 #include "fmm_queue.cuh"
+#include "fmm_fp64.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -113,21 +114,8 @@ __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ double vmin(double a, double b) { return lt(a, b) ? a : b; }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
-// Double square root: single-precision estimates y of sqrt(v) and rh of
-// 1/(2 sqrt(v)) refined by one Newton step in double, y + rh (v - y^2)
-// (relative error about 1e-14, far below the solver's tolerance; two double
-// FMAs keep most of the work off the FP64 pipe).  Values outside the float
-// range take the library square root.
-__device__ __forceinline__ double vsqrt(double v)
-{
-    const float vf = (float)v;
-    if (!(vf >= 1e-30f && vf <= 1e30f))
-        return sqrt(v);
-    const float rf = rsqrtf(vf);
-    const double y = (double)(vf * rf);
-    const double rh = (double)(0.5f * rf);
-    return fma(rh, fma(-y, y, v), y);
-}
+// Double square root without the FP64 pipe's slow conversions (fmm_fp64.cuh).
+__device__ __forceinline__ double vsqrt(double v) { return sqrt_fp64(v); }
 // Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance);
 // +inf (the speed term of an obstacle cell) stays +inf.
 __device__ __forceinline__ float vsqrt(float v)

@@ -130,13 +130,16 @@ __device__ __forceinline__ float vsqrt(float v)
 // with psi (in psi itself b^2 and 4ac would cancel to ~3 (psi F/h)^2 ulp).
 // The causality test psi_i < t is delta_i < u.  q is the cell's speed term.
 //
-// The per-axis values are sorted once (a stable sort, so equal values keep
-// the lower axis first and the higher axis is dropped first).  The smallest
-// has delta = 0, so only the other two enter S = sum delta_i and
-// Q = sum delta_i^2 (a dropped axis contributes 0): disc = S^2 - k (Q - q),
-// u = (S + sqrt(disc)) / k, causal when the largest remaining delta is below
-// u.  All lanes of a warp evaluate their full set together; a lane whose full
-// set is not causal (about 1% of solves) goes round the loop again.
+// Per axis the upwind value is the smaller known neighbour if it is below
+// Tc; with a tape (kTape) the side it came from is kept as well (the minus
+// side on a tie).  The per-axis values are sorted once (a stable sort, so
+// equal values keep the lower axis first and the higher axis is dropped
+// first).  The smallest has delta = 0, so only the other two enter
+// S = sum delta_i and Q = sum delta_i^2 (a dropped axis contributes 0):
+// disc = S^2 - k (Q - q), u = (S + sqrt(disc)) / k, causal when the largest
+// remaining delta is below u.  All lanes of a warp evaluate their full set
+// together; a lane whose full set is not causal (about 1% of solves) goes
+// round the loop again.
 template <typename real>
 __device__ __forceinline__ void cswap(real &a, unsigned &ca, real &b, unsigned &cb)
 {
@@ -150,7 +153,7 @@ __device__ __forceinline__ void cswap(real &a, unsigned &ca, real &b, unsigned &
     }
 }
 
-template <typename real>
+template <typename real, bool kTape>
 __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real q,
                                            uint8_t &set_out)
 {
@@ -162,14 +165,22 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
-        int d = 0;
-        if (lt(vm, Tc))
-            d = -1;
-        if (lt(vp, Tc) && (d == 0 || lt(vp, vm)))
-            d = 1;
-        v[a] = d == 0 ? INF : (d < 0 ? vm : vp);
-        code[a] = d == 0 ? 0u : (d < 0 ? 1u : 2u) << (2 * a);
-        nd += d != 0;
+        if (kTape) {
+            int d = 0;
+            if (lt(vm, Tc))
+                d = -1;
+            if (lt(vp, Tc) && (d == 0 || lt(vp, vm)))
+                d = 1;
+            v[a] = d == 0 ? INF : (d < 0 ? vm : vp);
+            code[a] = d == 0 ? 0u : (d < 0 ? 1u : 2u) << (2 * a);
+            nd += d != 0;
+        } else {
+            const real w = vmin(vm, vp);
+            const bool up = lt(w, Tc);
+            v[a] = up ? w : INF;
+            code[a] = 0u;
+            nd += up;
+        }
     }
     set_out = 0;
     if (nd == 0)
@@ -636,7 +647,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
                 ti = tile_of(c);
                 tc = W.tv[c];
                 const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
-                cand = solve_cell<real>(W.kv, ti, tc, sp, cset);
+                cand = solve_cell<real, kTape>(W.kv, ti, tc, sp, cset);
             }
             __syncwarp();
             // each cell appears once in the list, so tc is still its value

@@ -116,12 +116,10 @@ __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
 // Double square root without the FP64 pipe's slow conversions (fmm_fp64.cuh).
 __device__ __forceinline__ double vsqrt(double v) { return sqrt_fp64(v); }
-// Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance);
-// +inf (the speed term of an obstacle cell) stays +inf.
-__device__ __forceinline__ float vsqrt(float v)
-{
-    return v > 0.0f ? (v < CUDART_INF_F ? v * rsqrtf(v) : v) : 0.0f;
-}
+// Single precision: x * rsqrt(x) (a few ulp, far below the fp32 tolerance;
+// 0 stays 0).  The +inf speed term of an obstacle cell gives NaN, which fails
+// every causality test of Algorithm 11, so the cell's candidate is +inf.
+__device__ __forceinline__ float vsqrt(float v) { return v * rsqrtf(fmaxf(v, 1e-37f)); }
 
 // The quadratic of Algorithm 11, sum_i (t - psi_i)^2 / h^2 = 1/F^2 over the
 // upwind set, is solved for the unknown shifted by the smallest upwind value
@@ -185,10 +183,19 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
     set_out = 0;
     if (nd == 0)
         return INF;
-    // stable sort of three (adjacent compare-exchange, strict less-than)
-    cswap(v[0], code[0], v[1], code[1]);
-    cswap(v[1], code[1], v[2], code[2]);
-    cswap(v[0], code[0], v[1], code[1]);
+    if constexpr (!kTape && sizeof(real) == 4) {
+        // without sides to carry along: a min / max network
+        const float a = fminf(v[0], v[1]), b = fmaxf(v[0], v[1]);
+        const float d = fminf(b, v[2]);
+        v[2] = fmaxf(b, v[2]);
+        v[0] = fminf(a, d);
+        v[1] = fmaxf(a, d);
+    } else {
+        // stable sort of three (adjacent compare-exchange, strict less-than)
+        cswap(v[0], code[0], v[1], code[1]);
+        cswap(v[1], code[1], v[2], code[2]);
+        cswap(v[0], code[0], v[1], code[1]);
+    }
     const real m = v[0];
     real d1 = nd >= 2 ? v[1] - m : (real)0;
     real d2 = nd >= 3 ? v[2] - m : (real)0;

@@ -90,8 +90,15 @@ __device__ __forceinline__ int tb_of(int lx, int lr, int k)
 // Tape code of axis a of cell tp: 0 none, 1 minus neighbour, 2 plus.
 __device__ __forceinline__ int tape_axis(uint8_t tp, int a) { return (tp >> (2 * a)) & 3; }
 
-template <typename real>
-__device__ __forceinline__ bool is_nan(real v) { return v != v; }
+// NaN test and "> 0" for values that are >= 0 or NaN, on the bit patterns
+// (integer compares keep them off the FP64 pipe)
+__device__ __forceinline__ bool is_nan_bits(float v) { return (__float_as_uint(v) & 0x7fffffffu) > 0x7f800000u; }
+__device__ __forceinline__ bool is_nan_bits(double v)
+{
+    return (__double_as_longlong(v) & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool positive(float v) { return __float_as_int(v) > 0; }
+__device__ __forceinline__ bool positive(double v) { return __double_as_longlong(v) > 0; }
 
 // a / b and sqrt(v) for the adjoint; in double, float seeds refined by
 // Newton steps without the FP64 pipe's slow conversions (fmm_fp64.cuh).
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             // cells that were not accepted have no upwind set
             W.tp[ti] = accepted(tg) ? s.tape[base + c] : (uint8_t)0;
             W.tg[c] = tg;
-            todo |= (unsigned)(accepted(tg) && is_nan(m)) << k;
+            todo |= (unsigned)(accepted(tg) && is_nan_bits(m)) << k;
         }
         // ---- halo: the face layers of the six neighbours ------------------
 #pragma unroll
@@ -207,45 +214,48 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                     rest &= rest - 1u;
                 }
                 bool ready = false;
-                real lam = (real)0, dsum = (real)0;
                 int ti = 0;
                 if (k >= 0) {
+                    // ready when every downwind neighbour has published: on
+                    // axis a, q = p - e_a (its upwind code 2 points at p)
+                    // and q = p + e_a (code 1)
                     ti = tb_of(lx, lr, k);
                     ready = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int qm = ti - off[a], qp = ti + off[a];
+                        if (tape_axis(W.tp[qm], a) == 2 && is_nan_bits(W.mu[qm]))
+                            ready = false;
+                        if (tape_axis(W.tp[qp], a) == 1 && is_nan_bits(W.mu[qp]))
+                            ready = false;
+                    }
+                }
+                // the cells of this step test before any of them publishes
+                // (a published mu is final, so the sums below may read
+                // neighbours that other lanes publish in this step)
+                __syncwarp();
+                if (ready) {
+                    // the sums only for cells that are ready (the arithmetic
+                    // of the cells still waiting would be thrown away)
+                    real lam = (real)0, dsum = (real)0;
                     const real Tp = W.T[ti];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        // downwind neighbours on axis a: q = p - e_a (its
-                        // upwind code 2 points at p) and q = p + e_a (code 1)
                         const int qm = ti - off[a], qp = ti + off[a];
-                        if (tape_axis(W.tp[qm], a) == 2) {
-                            const real m = W.mu[qm];
-                            if (is_nan(m))
-                                ready = false;
-                            else
-                                lam += m * (W.T[qm] - Tp);
-                        }
-                        if (tape_axis(W.tp[qp], a) == 1) {
-                            const real m = W.mu[qp];
-                            if (is_nan(m))
-                                ready = false;
-                            else
-                                lam += m * (W.T[qp] - Tp);
-                        }
+                        if (tape_axis(W.tp[qm], a) == 2)
+                            lam += W.mu[qm] * (W.T[qm] - Tp);
+                        if (tape_axis(W.tp[qp], a) == 1)
+                            lam += W.mu[qp] * (W.T[qp] - Tp);
                         const int code = tape_axis(W.tp[ti], a);
                         if (code)
                             dsum += Tp - W.T[code == 1 ? qm : qp];
                     }
-                }
-                // the cells of this step read before any of them publishes
-                __syncwarp();
-                if (ready) {
                     const int c = lane + 32 * k;
                     const int cx = lx, cy = lr + 4 * (k & 1), cz = k >> 1;
                     const int i = bx * kB + cx, jj = by * kB + cy, kk = bz * kB + cz;
                     const long long nat = ((long long)kk * g.ny + jj) * g.nx + i;
                     lam += dLdT[nat];
-                    const real m = dsum > (real)0 ? adj_div(lam, dsum) : (real)0;
+                    const real m = positive(dsum) ? adj_div(lam, dsum) : (real)0;
                     W.mu[ti] = m;
                     // s_p h^2 = sqrt(q) h with q = (h/F)^2
                     const real sh2 = kHetero ? adj_sqrt(spd[base + c]) * (real)h : sh2_const;

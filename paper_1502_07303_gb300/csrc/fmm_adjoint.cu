@@ -26,6 +26,7 @@
 #include "fmm_internal.h"
 #include "fmm_queue.cuh"
 #include "fmm_fp64.cuh"
+#include "fmm_lanes.cuh"
 
 #include <cmath>
 
@@ -75,17 +76,6 @@ struct AdjTile {
     uint8_t tp[kTile3];  // tape of brick and halo
     uint8_t tg[kB3];     // tags of the brick
 };
-
-__device__ __forceinline__ int tile_of(int c)
-{
-    return 111 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
-}
-
-// Tile index of the cell k (0..15) of lane (lx, lr): x = lx, y = lr + 4 (k & 1), z = k / 2.
-__device__ __forceinline__ int tb_of(int lx, int lr, int k)
-{
-    return 111 + lx + kTile * (lr + 4 * (k & 1)) + kTile * kTile * (k >> 1);
-}
 
 // Tape code of axis a of cell tp: 0 none, 1 minus neighbour, 2 plus.
 __device__ __forceinline__ int tape_axis(uint8_t tp, int a) { return (tp >> (2 * a)) & 3; }
@@ -200,13 +190,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
         __syncwarp();
 
         // ---- rounds over the cells still to do ------------------------------
+        // The first round tests every cell still to do; later rounds only the
+        // neighbours of the cells done in the round before (a cell becomes
+        // ready when its last downwind neighbour is done; halo values are
+        // fixed for the pass).
         unsigned face_done = 0;   // bit f: a done cell has an upwind cell across face f
         unsigned done_any = 0;
+        unsigned cand = todo;
         for (;;) {
-            const int steps = (int)__reduce_max_sync(FULL, (unsigned)__popc(todo));
+            const int steps = (int)__reduce_max_sync(FULL, (unsigned)__popc(cand));
             if (steps == 0)
                 break;
-            unsigned rest = todo, done_now = 0;
+            unsigned rest = cand, done_now = 0;
             for (int j = 0; j < steps; ++j) {
                 int k = -1;
                 if (rest) {
@@ -276,6 +271,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             ++rounds_total;
             if (!__any_sync(FULL, done_now != 0u))
                 break;
+            cand = neighbour_mask(done_now, lane) & todo;
         }
         // ---- publish mu, wake the bricks that hold upwind neighbours ------
         for (unsigned mm = done_any; mm; mm &= mm - 1u) {

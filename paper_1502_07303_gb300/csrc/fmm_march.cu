@@ -39,6 +39,7 @@
 #include "fmm_internal.h"
 #include "fmm_queue.cuh"
 #include "fmm_fp64.cuh"
+#include "fmm_lanes.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -446,37 +447,6 @@ struct WarpTile {
     uint16_t list[kB3];    // compacted cells to solve
     unsigned improved[32]; // per owner lane: cells whose value dropped
 };
-
-__device__ __forceinline__ int tile_of(int c)
-{
-    return 111 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
-}
-
-// Cells of lane l next to a cell of the set A (16-bit lane masks).
-__device__ __forceinline__ unsigned neighbour_mask(unsigned A, int lane)
-{
-    const int x = lane & 7, r = (lane >> 3) & 3;
-    const unsigned axm = __shfl_up_sync(FULL, A, 1);
-    const unsigned axp = __shfl_down_sync(FULL, A, 1);
-    const unsigned aym = __shfl_up_sync(FULL, A, 8);
-    const unsigned ayp = __shfl_down_sync(FULL, A, 8);
-    const unsigned ay3 = __shfl_down_sync(FULL, A, 24);   // lanes 0..7 read row 3
-    const unsigned ay0 = __shfl_up_sync(FULL, A, 24);     // lanes 24..31 read row 0
-    unsigned n = (A << 2) | (A >> 2);                     // z -/+ 1
-    if (x > 0)
-        n |= axm;
-    if (x < 7)
-        n |= axp;
-    if (r > 0)
-        n |= aym;
-    if (r < 3)
-        n |= ayp;
-    if (r == 0)
-        n |= (ay3 << 1) & 0xAAAAu;     // y = 3 (slot k-1) -> y = 4 (odd slot k)
-    if (r == 3)
-        n |= (ay0 >> 1) & 0x5555u;     // y = 4 (slot k+1) -> y = 3 (even slot k)
-    return n & 0xFFFFu;
-}
 
 // Cells of lane l next to a halo cell flagged in the per-face masks F[6]
 // (face bit = u + 8 v with (u, v) the two in-face coordinates).

@@ -131,7 +131,7 @@ __device__ __forceinline__ float vsqrt(float v) { return v * rsqrtf(fmaxf(v, 1e-
 //
 // Per axis the upwind value is the smaller known neighbour if it is below
 // Tc; with a tape (kTape) the side it came from is kept as well (the minus
-// side on a tie).  The per-axis values are sorted once (a stable sort, so
+// side on a tie; without a tape the compiler drops the sides).  The per-axis values are sorted once (a stable sort, so
 // equal values keep the lower axis first and the higher axis is dropped
 // first).  The smallest has delta = 0, so only the other two enter
 // S = sum delta_i and Q = sum delta_i^2 (a dropped axis contributes 0):
@@ -164,22 +164,11 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
-        if (kTape) {
-            int d = 0;
-            if (lt(vm, Tc))
-                d = -1;
-            if (lt(vp, Tc) && (d == 0 || lt(vp, vm)))
-                d = 1;
-            v[a] = d == 0 ? INF : (d < 0 ? vm : vp);
-            code[a] = d == 0 ? 0u : (d < 0 ? 1u : 2u) << (2 * a);
-            nd += d != 0;
-        } else {
-            const real w = vmin(vm, vp);
-            const bool up = lt(w, Tc);
-            v[a] = up ? w : INF;
-            code[a] = 0u;
-            nd += up;
-        }
+        const real w = vmin(vm, vp);
+        const bool up = lt(w, Tc);
+        v[a] = up ? w : INF;
+        code[a] = up ? (lt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
+        nd += up;
     }
     set_out = 0;
     if (nd == 0)

@@ -185,6 +185,46 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
 fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness);
 
 /*
+ * fmm_resume -- continue a solve on hd that stopped at its restart limit
+ * (max_restarts) or wall-clock limit (timeout_s), or one loaded with
+ * fmm_checkpoint_load.  Such a solve ends on a restart boundary of
+ * Algorithm 16 (every brick marched to the last bound, no brick queued), so
+ * the loop simply goes on from that state, with its restart count,
+ * statistics and tape; the result is the one a single uninterrupted solve
+ * reaches.  more_restarts: restarts allowed from here (0 -> no limit; the
+ * wall-clock limit applies afresh).  T_out, tags_out as fmm_solve.
+ * FMM_ERR_STATE when the last solve finished, failed otherwise, or was
+ * followed by fmm_adjoint or fmm_set_speed (they reuse the control block);
+ * FMM_ERR_TIMEOUT again when a limit stops it once more.  (Resuming is not
+ * part of the paper.)
+ */
+fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_t *tags_out);
+
+/*
+ * Checkpoints of a solve state, in host memory: the brick-layout psi, tags,
+ * tape (when recorded), per-brick BAND minima, halo change masks and dirty
+ * flags, and the restart control block, after a 72-byte header that records
+ * the grid, dtype, h, record_tape and the kind of speed.
+ *   fmm_checkpoint_size -- bytes an image of hd takes (*bytes).
+ *   fmm_checkpoint_save -- write the image of the last solve on hd to
+ *     host_buf (host memory of at least that size, owned by the caller;
+ *     capacity its size).  The solve must have finished or stopped at a
+ *     limit (fmm_resume's condition); otherwise FMM_ERR_STATE.  Synchronises
+ *     hd's stream.
+ *   fmm_checkpoint_load -- load an image into hd, which must have been
+ *     created with the same grid, dtype, h, record_tape and kind of speed
+ *     (the speed values themselves, which the image does not hold, must be
+ *     the same too); else FMM_ERR_INVALID.  Afterwards hd is as the saving
+ *     handle was: fmm_resume continues a stopped solve, fmm_adjoint works on
+ *     a finished one with a tape.
+ * Batch handles have no checkpoints (FMM_ERR_STATE).  (Not part of the
+ * paper.)
+ */
+fmm_status fmm_checkpoint_size(fmm_handle *hd, int64_t *bytes);
+fmm_status fmm_checkpoint_save(fmm_handle *hd, void *host_buf, int64_t capacity);
+fmm_status fmm_checkpoint_load(fmm_handle *hd, const void *host_buf, int64_t size);
+
+/*
  * fmm_create_batch -- a solver for n_grids independent grids of uneven sizes
  * that are reinitialised together (speed F = 1): the bricks of all grids are
  * packed into one brick array, and with the persistent schedule (the

@@ -26,6 +26,9 @@ struct fmm_handle {
     Control *h_ctrl = nullptr;   // pinned host mirror of the control block
     bool solved = false;
     bool tape_valid = false;
+    bool resumable = false;           // stopped at the restart or time limit
+    bool complete = false;            // the last forward solve finished
+    Control fwd_ctrl;                 // its control block as it ended
     long long pre_launches = 0;       // init launches of the current solve
     fmm_stats stats;
     std::vector<cudaEvent_t> events;   // march timing pairs (time_kernels)
@@ -148,8 +151,11 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
         }
     }
     hd->tape_valid = false;
+    hd->resumable = false;
     return FMM_OK;
 }
+
+fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long long launches);
 
 // Algorithm 9, then the loop of Algorithm 16, then the output conversion.
 fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
@@ -158,14 +164,24 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     const Geom &g = hd->geom;
     const int dt = hd->cfg.dtype;
     cudaStream_t st = hd->stream;
+    hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
     FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
-    long long launches = 0;
     FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
-    launches += 2;   // control reset, front init
+    return run_restarts(hd, T_out, tags_out, 2);   // control reset, front init
+}
+
+// The loop of Algorithm 16 from the current state (a fresh initialisation or
+// the state after the last completed restart), then the output conversion.
+fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long long launches)
+{
+    DeviceState &s = hd->st;
+    const Geom &g = hd->geom;
+    const int dt = hd->cfg.dtype;
+    cudaStream_t st = hd->stream;
     const bool timing = hd->cfg.time_kernels != 0;
     size_t ev_used = 0;
     // The loop of Algorithm 16 runs on the device; the host enqueues restarts
@@ -270,7 +286,12 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
         }
     }
     hd->solved = true;
-    hd->tape_valid = s.tape != nullptr;
+    hd->complete = c.done && c.error == 0 && !timed_out;
+    hd->tape_valid = hd->complete && s.tape != nullptr;
+    // a solve stopped by the restart or wall-clock limit ends on a restart
+    // boundary: the state can be resumed (or saved and resumed elsewhere)
+    hd->resumable = !hd->complete && (timed_out ? c.error == 0 : c.error == ERR_RESTARTS);
+    hd->fwd_ctrl = c;
     if (timed_out)
         return fail(hd, FMM_ERR_TIMEOUT, "the solve exceeded its wall-clock limit (timeout_s)");
     if (c.error & ERR_ROUNDS)
@@ -283,6 +304,63 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Checkpoint image: this header, then T, tags, the tape (if recorded), the
+// per-brick BAND minima, the change masks and the dirty flags (the brick
+// layout of the device), then the control block the forward solve ended with.
+struct CkptHeader {
+    char magic[8];
+    int32_t version;
+    int32_t dtype;
+    int64_t nx, ny, nz;
+    double h;
+    int32_t record_tape;
+    int32_t hetero;
+    int32_t resumable;
+    int32_t complete;
+    int64_t bytes;
+};
+constexpr char kCkptMagic[8] = {'F', 'M', 'M', 'C', 'K', 'P', 'T', '1'};
+static_assert(sizeof(CkptHeader) == 72, "the header size fmm.h documents");
+
+struct CkptSection {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<CkptSection> ckpt_sections(fmm_handle *hd)
+{
+    DeviceState &s = hd->st;
+    const size_t nb = (size_t)hd->geom.nbricks, cells = nb * kB3;
+    std::vector<CkptSection> v = {{s.T, cells * hd->rsize}, {s.tag, cells}};
+    if (s.tape)
+        v.push_back({s.tape, cells});
+    v.push_back({s.bmin, 2 * nb * hd->rsize});
+    v.push_back({s.fresh, nb * kFaces * sizeof(unsigned long long)});
+    v.push_back({s.dirty, nb * sizeof(unsigned)});
+    return v;
+}
+
+int64_t ckpt_bytes(fmm_handle *hd)
+{
+    size_t n = sizeof(CkptHeader) + sizeof(Control);
+    for (const CkptSection &c : ckpt_sections(hd))
+        n += c.bytes;
+    return (int64_t)n;
+}
+
+void stats_from_control(fmm_handle *hd)
+{
+    const Control &c = hd->fwd_ctrl;
+    hd->stats.restarts = c.restart;
+    hd->stats.brick_marches = (int64_t)c.marches;
+    hd->stats.march_rounds = (int64_t)c.rounds;
+    hd->stats.exchanges = (int64_t)c.exchanges;
+    hd->stats.accepted = (int64_t)c.accepted;
+    hd->stats.cell_solves = (int64_t)c.solves;
+    hd->stats.n_bricks = hd->geom.nbricks;
+    hd->stats.error_flags = c.error;
+}
 
 }  // namespace
 
@@ -478,6 +556,7 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     a.spd_term = hd->params.spd_term;
     // every cell becomes ready once its downwind neighbours have published;
     // one persistent launch processes bricks until none is queued
+    hd->resumable = false;   // the adjoint reuses the control block and the flags
     FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
@@ -493,6 +572,132 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
         return fail(hd, FMM_ERR_TIMEOUT, "adjoint: a device wait exceeded its time limit");
     if (left != 0)
         return fail(hd, FMM_ERR_STATE, "adjoint: some accepted cells could not be ordered");
+    return FMM_OK;
+}
+
+fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_t *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!T_out || !aligned16(T_out))
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+    if (more_restarts < 0)
+        return fail(hd, FMM_ERR_INVALID, "more_restarts must be >= 0");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "a batch handle cannot resume");
+    if (!hd->resumable)
+        return fail(hd, FMM_ERR_STATE,
+                    "fmm_resume needs a solve stopped by its restart or time limit "
+                    "(or a loaded checkpoint of one)");
+    // the control block as the forward solve left it
+    Control &c = *hd->h_ctrl;
+    c = hd->fwd_ctrl;
+    c.done = 0;
+    c.error = 0;
+    const long long keep = hd->params.max_restarts;
+    hd->params.max_restarts = more_restarts > 0 ? (long long)c.restart + more_restarts : 0;
+    hd->resumable = false;
+    hd->pre_launches = 0;
+    cudaError_t e = cudaMemcpyAsync(hd->st.ctrl, hd->h_ctrl, sizeof(Control), cudaMemcpyHostToDevice,
+                                    hd->stream);
+    if (e != cudaSuccess) {
+        hd->params.max_restarts = keep;
+        return cuda_fail(hd, e, "fmm_resume: control block");
+    }
+    const fmm_status r = run_restarts(hd, T_out, tags_out, 0);
+    hd->params.max_restarts = keep;
+    return r;
+}
+
+fmm_status fmm_checkpoint_size(fmm_handle *hd, int64_t *bytes)
+{
+    if (!hd || !bytes)
+        return fail(hd, FMM_ERR_INVALID, "handle and bytes must not be NULL");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "batch handles have no checkpoint");
+    *bytes = ckpt_bytes(hd);
+    return FMM_OK;
+}
+
+fmm_status fmm_checkpoint_save(fmm_handle *hd, void *host_buf, int64_t capacity)
+{
+    if (!hd || !host_buf)
+        return fail(hd, FMM_ERR_INVALID, "handle and host_buf must not be NULL");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "batch handles have no checkpoint");
+    const int64_t need = ckpt_bytes(hd);
+    if (capacity < need)
+        return fail(hd, FMM_ERR_INVALID, "host_buf is smaller than fmm_checkpoint_size");
+    const bool complete = hd->solved && hd->complete;
+    if (!complete && !hd->resumable)
+        return fail(hd, FMM_ERR_STATE,
+                    "a checkpoint needs a finished solve or one stopped by its restart or time limit");
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    CkptHeader hdr;
+    memset(&hdr, 0, sizeof(hdr));
+    memcpy(hdr.magic, kCkptMagic, sizeof(hdr.magic));
+    hdr.version = 1;
+    hdr.dtype = hd->cfg.dtype;
+    hdr.nx = hd->geom.nx;
+    hdr.ny = hd->geom.ny;
+    hdr.nz = hd->geom.nz;
+    hdr.h = hd->params.h;
+    hdr.record_tape = hd->st.tape != nullptr;
+    hdr.hetero = hd->st.spd != nullptr;
+    hdr.resumable = hd->resumable;
+    hdr.complete = complete;
+    hdr.bytes = need;
+    unsigned char *p = (unsigned char *)host_buf;
+    memcpy(p, &hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    for (const CkptSection &c : ckpt_sections(hd)) {
+        FMM_CUDA(hd, cudaMemcpy(p, c.dev, c.bytes, cudaMemcpyDeviceToHost));
+        p += c.bytes;
+    }
+    memcpy(p, &hd->fwd_ctrl, sizeof(Control));
+    return FMM_OK;
+}
+
+fmm_status fmm_checkpoint_load(fmm_handle *hd, const void *host_buf, int64_t size)
+{
+    if (!hd || !host_buf)
+        return fail(hd, FMM_ERR_INVALID, "handle and host_buf must not be NULL");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "batch handles have no checkpoint");
+    CkptHeader hdr;
+    if (size < (int64_t)sizeof(hdr))
+        return fail(hd, FMM_ERR_INVALID, "checkpoint too short");
+    memcpy(&hdr, host_buf, sizeof(hdr));
+    if (memcmp(hdr.magic, kCkptMagic, sizeof(hdr.magic)) != 0 || hdr.version != 1)
+        return fail(hd, FMM_ERR_INVALID, "not a checkpoint of this library");
+    if (hdr.dtype != hd->cfg.dtype || hdr.nx != hd->geom.nx || hdr.ny != hd->geom.ny ||
+        hdr.nz != hd->geom.nz || hdr.h != hd->params.h)
+        return fail(hd, FMM_ERR_INVALID, "checkpoint grid or dtype differs from the handle's");
+    if ((hdr.record_tape != 0) != (hd->st.tape != nullptr) || (hdr.hetero != 0) != (hd->st.spd != nullptr))
+        return fail(hd, FMM_ERR_INVALID, "checkpoint record_tape or speed kind differs from the handle's");
+    if (hdr.bytes != ckpt_bytes(hd) || size < hdr.bytes)
+        return fail(hd, FMM_ERR_INVALID, "checkpoint size does not match the handle");
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    const unsigned char *p = (const unsigned char *)host_buf + sizeof(hdr);
+    for (const CkptSection &c : ckpt_sections(hd)) {
+        FMM_CUDA(hd, cudaMemcpy(c.dev, p, c.bytes, cudaMemcpyHostToDevice));
+        p += c.bytes;
+    }
+    memcpy(&hd->fwd_ctrl, p, sizeof(Control));
+    // this process's wait limit and testing flag, not the saver's
+    hd->fwd_ctrl.wait_ns = hd->params.wait_ns;
+    hd->fwd_ctrl.hold = hd->params.hold;
+    *hd->h_ctrl = hd->fwd_ctrl;
+    FMM_CUDA(hd, cudaMemcpy(hd->st.ctrl, hd->h_ctrl, sizeof(Control), cudaMemcpyHostToDevice));
+    // the queue is empty between restarts
+    const Geom &g = hd->geom;
+    FMM_CUDA(hd, cudaMemset(hd->st.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long)));
+    FMM_CUDA(hd, cudaMemset(hd->st.queued, 0, (size_t)g.nbricks * sizeof(unsigned)));
+    hd->complete = hdr.complete != 0;
+    hd->resumable = hdr.resumable != 0;
+    hd->solved = hd->complete || hd->resumable;
+    hd->tape_valid = hd->complete && hd->st.tape != nullptr;
+    stats_from_control(hd);
     return FMM_OK;
 }
 

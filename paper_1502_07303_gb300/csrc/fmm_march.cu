@@ -952,7 +952,9 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // works as a sequence lock: odd while a raise rewrites the bound and the scan
 // counters.  The solve is complete when no raise is in progress, the last
 // scan is done, nothing is queued or marching and the bound has reached width
-// on both sides.  Every wait is bounded (wait_ns without any progress).
+// on both sides.  At the restart limit the raises stop and the launch ends
+// once the current level is drained, so the solve can be resumed from there.
+// Every wait is bounded (wait_ns without any progress).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double vloadd(const double *p) { return *(const volatile double *)p; }
@@ -1090,7 +1092,11 @@ __device__ bool try_raise(Control *c, const SolveParams &p, int nchunks, int pen
 }
 
 // The solve is complete (lane 0; see above).
-__device__ bool solve_complete(Control *c, const SolveParams &p, int nchunks)
+// The launch ends when the solve is complete or, once the restart limit has
+// stopped the raises (limited), when the current level is drained: no raise
+// or scan in progress and nothing queued or marching.  The state is then the
+// one after a restart of Algorithm 16, from which a solve can resume.
+__device__ bool launch_done(Control *c, const SolveParams &p, int nchunks, bool limited)
 {
     const int e = vload(&c->epoch);
     if ((e & 1) || vload(&c->scan_done) < nchunks)
@@ -1098,7 +1104,7 @@ __device__ bool solve_complete(Control *c, const SolveParams &p, int nchunks)
     __threadfence();
     if (vload(&c->pending) != 0)
         return false;
-    if (vloadd(&c->bound[0]) < p.width || vloadd(&c->bound[1]) < p.width)
+    if (!limited && (vloadd(&c->bound[0]) < p.width || vloadd(&c->bound[1]) < p.width))
         return false;
     __threadfence();
     return vload(&c->epoch) == e;
@@ -1128,10 +1134,12 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
             arg = (long long)(v & 0xffffffffull) - 1;
             return;
         }
-        if (vload(&c->error) & (ERR_SPIN | ERR_RESTARTS)) {
+        const int err = vload(&c->error);
+        if (err & ERR_SPIN) {
             job = 2;
             return;
         }
+        const bool limited = (err & ERR_RESTARTS) != 0;
         if (vload(&c->scan_next) < nchunks) {
             const int ch = atomicAdd(&c->scan_next, 1);
             if (ch < nchunks) {
@@ -1141,9 +1149,9 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
             }
         }
         const int pend = vload(&c->pending);
-        if (pend < p.raise_at && try_raise(c, p, nchunks, pend))
+        if (!limited && pend < p.raise_at && try_raise(c, p, nchunks, pend))
             continue;
-        if (pend == 0 && solve_complete(c, p, nchunks)) {
+        if (pend == 0 && launch_done(c, p, nchunks, limited)) {
             job = 2;
             return;
         }

@@ -94,9 +94,14 @@ def load(path: str | None = None):
                                      ctypes.POINTER(vp)]
     lib.fmm_reinit_batch.argtypes = [vp, vp, vp, vp]
     lib.fmm_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.fmm_resume.argtypes = [vp, i64, vp, vp]
+    lib.fmm_checkpoint_size.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.fmm_checkpoint_save.argtypes = [vp, vp, i64]
+    lib.fmm_checkpoint_load.argtypes = [vp, vp, i64]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
               "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
-              "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace"):
+              "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace", "fmm_resume",
+              "fmm_checkpoint_size", "fmm_checkpoint_save", "fmm_checkpoint_load"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -211,6 +216,27 @@ class Solver:
         T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
         self._check(self.lib.fmm_reinit_signed_distance(self.handle, pp, tp, gp))
         return T_out, tags_out
+
+    def resume(self, T_out=None, tags_out=None, want_tags=True, more_restarts=0):
+        """Continue a solve stopped by max_restarts or timeout_s (or loaded
+        with restore); more_restarts=0 means no further limit."""
+        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
+        self._check(self.lib.fmm_resume(self.handle, int(more_restarts), tp, gp))
+        return T_out, tags_out
+
+    def checkpoint(self):
+        """Host image (numpy uint8) of the last solve's state."""
+        n = ctypes.c_int64(0)
+        self._check(self.lib.fmm_checkpoint_size(self.handle, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._check(self.lib.fmm_checkpoint_save(self.handle, buf.ctypes.data, n.value))
+        return buf
+
+    def restore(self, image):
+        """Load an image written by checkpoint() of a handle with the same grid,
+        dtype, h, record_tape and speed."""
+        buf = np.ascontiguousarray(np.asarray(image, dtype=np.uint8))
+        self._check(self.lib.fmm_checkpoint_load(self.handle, buf.ctypes.data, buf.size))
 
     def adjoint(self, dL_dT, out=None):
         gp = _dev_ptr(dL_dT, self.dtype, self.shape, "dL_dT")

@@ -19,7 +19,10 @@ parallel fast marching method for the Eikonal equation"):
 * ``adjoint`` / ``tangent``           -- derivatives of the discrete Eq. (2)
   about the final upwind sets (not in the paper; derived from Eq. (2)-(3))
 
-Arrays are numpy arrays of shape (nz, ny, nx) in C order (x fastest).
+Arrays are numpy arrays of shape (nz, ny, nx) in C order (x fastest).  The
+spacing ``h`` is one cell size for every axis or a 3-sequence (dx, dy, dz):
+the cells of Sec. 2.1 are uniform in each direction, and Algorithm 11 takes
+one h_i per axis.
 """
 from __future__ import annotations
 
@@ -112,16 +115,16 @@ def _bind(lib):
     i64, dbl = ctypes.c_int64, ctypes.c_double
     vp = ctypes.c_void_p
     lib.oracle_init_sources.argtypes = [i64, i64, i64, vp, i64, vp, vp]
-    lib.oracle_init_reinit.argtypes = [i64, i64, i64, dbl, vp, vp, vp]
-    lib.oracle_march.argtypes = [i64, i64, i64, dbl, vp, dbl, dbl, vp, vp,
+    lib.oracle_init_reinit.argtypes = [i64, i64, i64, vp, vp, vp, vp]
+    lib.oracle_march.argtypes = [i64, i64, i64, vp, vp, dbl, dbl, vp, vp,
                                  vp, vp, vp]
-    lib.oracle_local_solve.argtypes = [vp, vp, dbl, dbl, dbl]
+    lib.oracle_local_solve.argtypes = [vp, vp, dbl, vp, dbl]
     lib.oracle_local_solve.restype = dbl
-    lib.oracle_fast_sweep.argtypes = [i64, i64, i64, dbl, vp, dbl, vp, vp,
+    lib.oracle_fast_sweep.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp,
                                       i64, vp]
-    lib.oracle_adjoint.argtypes = [i64, i64, i64, dbl, vp, dbl, vp, vp, vp,
+    lib.oracle_adjoint.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp, vp,
                                    vp, i64, vp, vp, vp]
-    lib.oracle_tangent.argtypes = [i64, i64, i64, dbl, vp, dbl, vp, vp, vp,
+    lib.oracle_tangent.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp, vp,
                                    vp, i64, vp, vp]
     for name in ("oracle_init_sources", "oracle_init_reinit", "oracle_march",
                  "oracle_fast_sweep", "oracle_adjoint", "oracle_tangent"):
@@ -136,6 +139,13 @@ def _ptr(a):
 def _check(rc, what):
     if rc != 0:
         raise ValueError(f"{what} failed with code {rc}")
+
+
+def _spacing(h):
+    """(dx, dy, dz) as a C array: h is one cell size for all axes or a
+    3-sequence (dx, dy, dz)."""
+    h3 = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (3,)))
+    return h3
 
 
 def _speed_args(speed, shape):
@@ -166,7 +176,8 @@ def init_reinit(phi0, h):
     nz, ny, nx = phi.shape
     T = np.empty(phi.shape, np.float64)
     G = np.empty(phi.shape, np.uint8)
-    _check(_load().oracle_init_reinit(nx, ny, nz, float(h), _ptr(phi), _ptr(T),
+    h3 = _spacing(h)
+    _check(_load().oracle_init_reinit(nx, ny, nz, _ptr(h3), _ptr(phi), _ptr(T),
                                       _ptr(G)), "init_reinit")
     return T, G
 
@@ -184,7 +195,8 @@ def march(T, G, h, speed=None, width=np.inf, record=False):
     order = np.empty(n, np.int64) if record else None
     tape = np.empty(T.shape, np.uint8) if record else None
     n_order = ctypes.c_int64(0)
-    _check(_load().oracle_march(nx, ny, nz, float(h), _ptr(sp), sc, float(width),
+    h3 = _spacing(h)
+    _check(_load().oracle_march(nx, ny, nz, _ptr(h3), _ptr(sp), sc, float(width),
                                 _ptr(T), _ptr(G), _ptr(order),
                                 ctypes.addressof(n_order), _ptr(tape)), "march")
     out = {"T": T, "G": G, "n_accepted": int(n_order.value)}
@@ -209,8 +221,9 @@ def local_solve(nb, nb_known, Tc, h, F):
     nb = np.ascontiguousarray(nb, dtype=np.float64)
     kn = np.ascontiguousarray(nb_known, dtype=np.uint8)
     assert nb.shape == (6,) and kn.shape == (6,)
+    h3 = _spacing(h)
     return float(_load().oracle_local_solve(_ptr(nb), _ptr(kn), float(Tc),
-                                            float(h), float(F)))
+                                            _ptr(h3), float(F)))
 
 
 def fast_sweep(A0, fixed, h, speed=None, max_rounds=10000):
@@ -222,7 +235,8 @@ def fast_sweep(A0, fixed, h, speed=None, max_rounds=10000):
     nz, ny, nx = A.shape
     sp, sc = _speed_args(speed, A.shape)
     rounds = ctypes.c_int64(0)
-    _check(_load().oracle_fast_sweep(nx, ny, nz, float(h), _ptr(sp), sc, _ptr(A),
+    h3 = _spacing(h)
+    _check(_load().oracle_fast_sweep(nx, ny, nz, _ptr(h3), _ptr(sp), sc, _ptr(A),
                                      _ptr(fx), int(max_rounds),
                                      ctypes.addressof(rounds)), "fast_sweep")
     return A, int(rounds.value)
@@ -237,7 +251,8 @@ def adjoint(res, h, dLdT, speed=None):
     g = np.ascontiguousarray(dLdT, dtype=np.float64)
     dLds = np.empty(T.shape, np.float64)
     lam = np.empty(T.shape, np.float64)
-    _check(_load().oracle_adjoint(nx, ny, nz, float(h), _ptr(sp), sc, _ptr(T),
+    h3 = _spacing(h)
+    _check(_load().oracle_adjoint(nx, ny, nz, _ptr(h3), _ptr(sp), sc, _ptr(T),
                                   _ptr(G), _ptr(tape), _ptr(order), len(order),
                                   _ptr(g), _ptr(dLds), _ptr(lam)), "adjoint")
     return dLds, lam
@@ -250,7 +265,8 @@ def tangent(res, h, v, speed=None):
     sp, sc = _speed_args(speed, T.shape)
     vv = np.ascontiguousarray(v, dtype=np.float64)
     dT = np.empty(T.shape, np.float64)
-    _check(_load().oracle_tangent(nx, ny, nz, float(h), _ptr(sp), sc, _ptr(T),
+    h3 = _spacing(h)
+    _check(_load().oracle_tangent(nx, ny, nz, _ptr(h3), _ptr(sp), sc, _ptr(T),
                                   _ptr(G), _ptr(tape), _ptr(order), len(order),
                                   _ptr(vv), _ptr(dT)), "tangent")
     return dT

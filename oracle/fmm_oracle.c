@@ -23,6 +23,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* the cell sizes (dx, dy, dz) of Sec. 2.1 must be positive */
+static int spacing_ok(const double h3[3])
+{
+    return h3 && h3[0] > 0 && h3[1] > 0 && h3[2] > 0;
+}
+
 #define OR_INF INFINITY
 
 static int is_known(uint8_t g)
@@ -108,11 +114,11 @@ int oracle_init_sources(int64_t nx, int64_t ny, int64_t nz,
     return 0;
 }
 
-int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                        const double *phi0, double *T, uint8_t *G)
 {
     grid_t g;
-    if (grid_make(&g, nx, ny, nz) || !phi0 || !T || !G || !(h > 0))
+    if (grid_make(&g, nx, ny, nz) || !phi0 || !T || !G || !spacing_ok(h3))
         return -1;
     for (int64_t p = 0; p < g.n; ++p) {
         int64_t c[3];
@@ -133,7 +139,7 @@ int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, double h,
                 /* the interface crosses the segment p-q at fraction theta
                  * of the way from p (linear interpolation of phi0) */
                 double theta = fc / (fc - fq);
-                double dist = theta * h;
+                double dist = theta * h3[a];
                 if (dist < d_axis[a])
                     d_axis[a] = dist;
                 any = 1;
@@ -172,7 +178,7 @@ typedef struct {
 
 typedef struct {
     grid_t g;
-    double h;
+    double h3[3];       /* dx, dy, dz */
     const double *speed;
     double speed_const;
     double *T;
@@ -352,7 +358,7 @@ static double solve_quadratic(const march_t *m, int64_t l, uint8_t *set_out)
         dir[a] = d;
         if (d != 0) {
             psi[a] = fabs(m->T[l + d * g->stride[a]]);
-            hh[a] = 1.0 / m->h;
+            hh[a] = 1.0 / m->h3[a];
         } else {
             psi[a] = 0.0;
             hh[a] = 0.0;
@@ -364,7 +370,7 @@ static double solve_quadratic(const march_t *m, int64_t l, uint8_t *set_out)
 }
 
 double oracle_local_solve(const double nb[6], const uint8_t nb_known[6],
-                          double Tc, double h, double F)
+                          double Tc, const double h3[3], double F)
 {
     double psi[3], hh[3];
     int dir[3];
@@ -383,7 +389,7 @@ double oracle_local_solve(const double nb[6], const uint8_t nb_known[6],
         dir[a] = d;
         if (d != 0) {
             psi[a] = (d < 0) ? vm : vp;
-            hh[a] = 1.0 / h;
+            hh[a] = 1.0 / h3[a];
         } else {
             psi[a] = 0.0;
             hh[a] = 0.0;
@@ -440,20 +446,21 @@ static int update_neighbors(march_t *m, int64_t idx, int s)
 /* Algorithm 9 + Algorithm 12 with bound = width                              */
 /* ------------------------------------------------------------------------ */
 
-int oracle_march(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                  const double *speed, double speed_const, double width,
                  double *T, uint8_t *G,
                  int64_t *order, int64_t *n_order, uint8_t *tape)
 {
     march_t m;
     memset(&m, 0, sizeof(m));
-    if (grid_make(&m.g, nx, ny, nz) || !T || !G || !(h > 0))
+    if (grid_make(&m.g, nx, ny, nz) || !T || !G || !spacing_ok(h3))
         return -1;
     if (m.g.n >= (int64_t)2147483647)
         return -1;
     if (!speed && !(speed_const > 0))
         return -1;
-    m.h = h;
+    for (int a = 0; a < 3; ++a)
+        m.h3[a] = h3[a];
     m.speed = speed;
     m.speed_const = speed_const;
     m.T = T;
@@ -514,28 +521,32 @@ int oracle_march(int64_t nx, int64_t ny, int64_t nz, double h,
 /* Fast sweeping with the textbook sorted Godunov update                      */
 /* ------------------------------------------------------------------------ */
 
-/* Unique t with sum_i max(t - a_i, 0)^2 = (s h)^2 for a1 <= a2 <= a3. */
-static double godunov_sorted(double a1, double a2, double a3, double sh)
+/* Unique t with sum_i max(t - a_i, 0)^2 / h_i^2 = s^2 for a1 <= a2 <= a3
+ * (the values sorted with their cell sizes): take the first 1, 2 or 3 terms
+ * while the root exceeds the next value.  With c_i = 1/h_i^2 the k-term
+ * equation is (sum c) t^2 - 2 (sum c a) t + (sum c a^2) - s^2 = 0. */
+static double godunov_sorted(const double a[3], const double hs[3], double s)
 {
-    double t = a1 + sh;
-    if (t <= a2)
-        return t;
-    double d = a1 - a2;
-    t = 0.5 * (a1 + a2 + sqrt(2.0 * sh * sh - d * d));
-    if (t <= a3)
-        return t;
-    double S = a1 + a2 + a3;
-    double Q = a1 * a1 + a2 * a2 + a3 * a3;
-    return (S + sqrt(S * S - 3.0 * (Q - sh * sh))) / 3.0;
+    double C = 0.0, B = 0.0, A2 = 0.0, t = OR_INF;
+    for (int k = 0; k < 3; ++k) {
+        if (a[k] == OR_INF || (k > 0 && t <= a[k]))
+            break;
+        double c = 1.0 / (hs[k] * hs[k]);
+        C += c;
+        B += c * a[k];
+        A2 += c * a[k] * a[k];
+        t = (B + sqrt(B * B - C * (A2 - s * s))) / C;
+    }
+    return t;
 }
 
-int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                       const double *speed, double speed_const,
                       double *A, const uint8_t *fixed,
                       int64_t max_rounds, int64_t *rounds_out)
 {
     grid_t g;
-    if (grid_make(&g, nx, ny, nz) || !A || !fixed || !(h > 0))
+    if (grid_make(&g, nx, ny, nz) || !A || !fixed || !spacing_ok(h3))
         return -1;
     int64_t rounds = 0;
     for (; rounds < max_rounds;) {
@@ -552,7 +563,7 @@ int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, double h,
                         int64_t p = (k * ny + j) * nx + i;
                         if (fixed[p])
                             continue;
-                        double a[3];
+                        double a[3], hs[3];
                         int64_t c[3] = {i, j, k};
                         for (int ax = 0; ax < 3; ++ax) {
                             double v = OR_INF;
@@ -563,15 +574,19 @@ int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, double h,
                             if (qp >= 0 && A[qp] < v)
                                 v = A[qp];
                             a[ax] = v;
+                            hs[ax] = h3[ax];
                         }
-                        /* sort ascending */
-                        if (a[0] > a[1]) { double t = a[0]; a[0] = a[1]; a[1] = t; }
-                        if (a[1] > a[2]) { double t = a[1]; a[1] = a[2]; a[2] = t; }
-                        if (a[0] > a[1]) { double t = a[0]; a[0] = a[1]; a[1] = t; }
+                        /* sort ascending, each cell size with its value */
+                        for (int pass = 0; pass < 2; ++pass)
+                            for (int q = 0; q < 2; ++q)
+                                if (a[q] > a[q + 1]) {
+                                    double t = a[q]; a[q] = a[q + 1]; a[q + 1] = t;
+                                    t = hs[q]; hs[q] = hs[q + 1]; hs[q + 1] = t;
+                                }
                         if (a[0] == OR_INF)
                             continue;
                         double F = speed_at(speed, speed_const, p);
-                        double t = godunov_sorted(a[0], a[1], a[2], h / F);
+                        double t = godunov_sorted(a, hs, 1.0 / F);
                         if (t < A[p]) {
                             A[p] = t;
                             changed = 1;
@@ -593,10 +608,10 @@ int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, double h,
 /* Linearisation about the final upwind sets (adjoint and tangent)            */
 /* ------------------------------------------------------------------------ */
 
-/* Upwind neighbours of p recorded in the tape: fills nbr[] and returns the
- * count. */
+/* Upwind neighbours of p recorded in the tape: fills nbr[] (and their axes
+ * in ax[]) and returns the count. */
 static int tape_neighbours(const grid_t *g, int64_t p, uint8_t set,
-                           int64_t nbr[3])
+                           int64_t nbr[3], int ax[3])
 {
     int64_t c[3];
     grid_coord(g, p, c);
@@ -606,13 +621,15 @@ static int tape_neighbours(const grid_t *g, int64_t p, uint8_t set,
         if (code == 0)
             continue;
         int64_t q = grid_nb(g, p, c, a, code == 1 ? -1 : 1);
-        if (q >= 0)
+        if (q >= 0) {
+            ax[n] = a;
             nbr[n++] = q;
+        }
     }
     return n;
 }
 
-int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                    const double *speed, double speed_const,
                    const double *T, const uint8_t *G, const uint8_t *tape,
                    const int64_t *order, int64_t n_order,
@@ -620,7 +637,7 @@ int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, double h,
 {
     grid_t g;
     if (grid_make(&g, nx, ny, nz) || !T || !G || !tape || !order || !dLdT ||
-        !dLds || !(h > 0))
+        !dLds || !spacing_ok(h3))
         return -1;
     double *lam = lambda ? lambda
                          : (double *)malloc((size_t)g.n * sizeof(double));
@@ -630,30 +647,31 @@ int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, double h,
         lam[p] = dLdT[p];
         dLds[p] = 0.0;
     }
-    double w = 1.0 / (h * h);
+    const double w[3] = {1.0 / (h3[0] * h3[0]), 1.0 / (h3[1] * h3[1]), 1.0 / (h3[2] * h3[2])};
     for (int64_t k = n_order - 1; k >= 0; --k) {
         int64_t p = order[k];
         if (G[p] == ORC_KNOWN_FIX)
             continue;
         int64_t nbr[3];
-        int nn = tape_neighbours(&g, p, tape[p], nbr);
+        int ax[3];
+        int nn = tape_neighbours(&g, p, tape[p], nbr, ax);
         if (nn == 0)
             continue;
         double Tp = fabs(T[p]);
         double D = 0.0;
         for (int q = 0; q < nn; ++q)
-            D += (Tp - fabs(T[nbr[q]])) * w;
+            D += (Tp - fabs(T[nbr[q]])) * w[ax[q]];
         double sp = 1.0 / speed_at(speed, speed_const, p);
         dLds[p] = lam[p] * sp / D;
         for (int q = 0; q < nn; ++q)
-            lam[nbr[q]] += lam[p] * (Tp - fabs(T[nbr[q]])) * w / D;
+            lam[nbr[q]] += lam[p] * (Tp - fabs(T[nbr[q]])) * w[ax[q]] / D;
     }
     if (!lambda)
         free(lam);
     return 0;
 }
 
-int oracle_tangent(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_tangent(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                    const double *speed, double speed_const,
                    const double *T, const uint8_t *G, const uint8_t *tape,
                    const int64_t *order, int64_t n_order,
@@ -661,23 +679,24 @@ int oracle_tangent(int64_t nx, int64_t ny, int64_t nz, double h,
 {
     grid_t g;
     if (grid_make(&g, nx, ny, nz) || !T || !G || !tape || !order || !v ||
-        !dT || !(h > 0))
+        !dT || !spacing_ok(h3))
         return -1;
     for (int64_t p = 0; p < g.n; ++p)
         dT[p] = 0.0;
-    double w = 1.0 / (h * h);
+    const double w[3] = {1.0 / (h3[0] * h3[0]), 1.0 / (h3[1] * h3[1]), 1.0 / (h3[2] * h3[2])};
     for (int64_t k = 0; k < n_order; ++k) {
         int64_t p = order[k];
         if (G[p] == ORC_KNOWN_FIX)
             continue;
         int64_t nbr[3];
-        int nn = tape_neighbours(&g, p, tape[p], nbr);
+        int ax[3];
+        int nn = tape_neighbours(&g, p, tape[p], nbr, ax);
         if (nn == 0)
             continue;
         double Tp = fabs(T[p]);
         double D = 0.0, acc = 0.0;
         for (int q = 0; q < nn; ++q) {
-            double c = (Tp - fabs(T[nbr[q]])) * w;
+            double c = (Tp - fabs(T[nbr[q]])) * w[ax[q]];
             D += c;
             acc += c * dT[nbr[q]];
         }

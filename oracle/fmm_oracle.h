@@ -6,9 +6,10 @@
  * check of the build entry point and the CPU-baseline leg of the benchmark may
  * load it.  It shares no code, header, table or helper with the CUDA library.
  *
- * Grid convention (Sec. 2.1): psi lives at cell centres of a uniform grid with
- * spacing h in every direction; arrays are nx*ny*nz doubles, x fastest:
- * idx = (k*ny + j)*nx + i.  Neighbours outside the grid are simply absent
+ * Grid convention (Sec. 2.1): psi lives at the centres of cells of size
+ * dx * dy * dz, uniform in each direction; h3 = {dx, dy, dz} (all > 0) gives
+ * the h_i = 1/dx, 1/dy, 1/dz of Algorithm 11.  Arrays are nx*ny*nz doubles,
+ * x fastest: idx = (k*ny + j)*nx + i.  Neighbours outside the grid are simply absent
  * (Sec. 4.1: no boundary conditions, stencils never leave the array).
  *
  * Tags are the augmented status tags of Sec. 4.2.  In a single-process run
@@ -44,9 +45,10 @@ int oracle_init_sources(int64_t nx, int64_t ny, int64_t nz,
 /* Algorithm 8 for a signed level set phi0: cells that have a 6-neighbour of
  * the opposite sign (sign(0) = +1) are the cells adjacent to the interface.
  * They get psi = sign * (sum over crossing axes of d_a^-2)^(-1/2), where d_a
- * is the smaller linear-interpolation crossing distance on axis a, and
- * KNOWN_FIX.  Every other cell gets +inf and FAR (Algorithm 8 assigns +inf). */
-int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, double h,
+ * is the smaller linear-interpolation crossing distance on axis a (a fraction
+ * of that axis's cell size), and KNOWN_FIX.  Every other cell gets +inf and
+ * FAR (Algorithm 8 assigns +inf). */
+int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                        const double *phi0, double *T, uint8_t *G);
 
 /* Algorithm 9 followed by Algorithm 12 with bound_band(+-1) = width (the
@@ -59,7 +61,7 @@ int oracle_init_reinit(int64_t nx, int64_t ny, int64_t nz, double h,
  *   tape[n]    : for each cell, the upwind set of the root that gave its final
  *                value: 2 bits per axis (x bits 0-1, y 2-3, z 4-5),
  *                0 = axis unused, 1 = minus neighbour, 2 = plus neighbour. */
-int oracle_march(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                  const double *speed, double speed_const, double width,
                  double *T, uint8_t *G,
                  int64_t *order, int64_t *n_order, uint8_t *tape);
@@ -69,27 +71,29 @@ int oracle_march(int64_t nx, int64_t ny, int64_t nz, double h,
  * KNOWN.  Tc is the cell's current |psi| (the upwind filter of Algorithm 11);
  * F is the speed at the cell.  Returns psi_temp (+inf if no causal root). */
 double oracle_local_solve(const double nb[6], const uint8_t nb_known[6],
-                          double Tc, double h, double F);
+                          double Tc, const double h3[3], double F);
 
 /* Gauss-Seidel fast sweeping (Zhao 2005, cited in Sec. 1) with the textbook
- * sorted Godunov update of Eq. (2) over all six neighbours.  A holds |psi|:
+ * sorted Godunov update of Eq. (2) over all six neighbours (the per-axis
+ * minima sorted together with their cell sizes).  A holds |psi|:
  * cells with fixed[idx] != 0 keep their value, the rest start at +inf.
  * Sweeps in the 8 alternating orders until a full round changes nothing or
  * max_rounds rounds are done; *rounds_out receives the count. */
-int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_fast_sweep(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                       const double *speed, double speed_const,
                       double *A, const uint8_t *fixed,
                       int64_t max_rounds, int64_t *rounds_out);
 
 /* Reverse-mode derivative of L(T) with respect to the slowness s = 1/F, with
  * the upwind sets of the tape held fixed.  At an accepted non-FIX cell p the
- * discrete equation sum_{i in U(p)} ((T_p - T_i)/h)^2 = s_p^2 gives
- *   dT_p/ds_p = s_p / D_p,  dT_p/dT_i = (T_p - T_i)/(h^2 D_p),
- *   D_p = sum_{i in U(p)} (T_p - T_i)/h^2,
+ * discrete equation sum_{i in U(p)} ((T_p - T_i)/h_i)^2 = s_p^2 (h_i the cell
+ * size along the axis of neighbour i) gives
+ *   dT_p/ds_p = s_p / D_p,  dT_p/dT_i = (T_p - T_i)/(h_i^2 D_p),
+ *   D_p = sum_{i in U(p)} (T_p - T_i)/h_i^2,
  * applied in reverse acceptance order.  FIX cells absorb lambda.  Inputs are
  * the outputs of oracle_march (|T| is used, so both sides work).
  * lambda (nullable) receives the total adjoint dL/dT_p. */
-int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                    const double *speed, double speed_const,
                    const double *T, const uint8_t *G, const uint8_t *tape,
                    const int64_t *order, int64_t n_order,
@@ -97,7 +101,7 @@ int oracle_adjoint(int64_t nx, int64_t ny, int64_t nz, double h,
 
 /* Forward-mode tangent dT = J v for a slowness perturbation v, with the same
  * linearisation as oracle_adjoint, applied in acceptance order. */
-int oracle_tangent(int64_t nx, int64_t ny, int64_t nz, double h,
+int oracle_tangent(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
                    const double *speed, double speed_const,
                    const double *T, const uint8_t *G, const uint8_t *tape,
                    const int64_t *order, int64_t n_order,

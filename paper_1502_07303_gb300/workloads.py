@@ -37,16 +37,18 @@ def spacing(shape):
 
 
 def _axes(shape, h, device=None):
+    """Cell-centre coordinates; h is one cell size or (dx, dy, dz)."""
     nz, ny, nx = shape
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else (float(v) for v in h)
     if device is None:
-        x = (np.arange(nx, dtype=np.float64) + 0.5) * h
-        y = (np.arange(ny, dtype=np.float64) + 0.5) * h
-        z = (np.arange(nz, dtype=np.float64) + 0.5) * h
+        x = (np.arange(nx, dtype=np.float64) + 0.5) * hx
+        y = (np.arange(ny, dtype=np.float64) + 0.5) * hy
+        z = (np.arange(nz, dtype=np.float64) + 0.5) * hz
         return x[None, None, :], y[None, :, None], z[:, None, None]
     import torch
-    x = (torch.arange(nx, dtype=torch.float64, device=device) + 0.5) * h
-    y = (torch.arange(ny, dtype=torch.float64, device=device) + 0.5) * h
-    z = (torch.arange(nz, dtype=torch.float64, device=device) + 0.5) * h
+    x = (torch.arange(nx, dtype=torch.float64, device=device) + 0.5) * hx
+    y = (torch.arange(ny, dtype=torch.float64, device=device) + 0.5) * hy
+    z = (torch.arange(nz, dtype=torch.float64, device=device) + 0.5) * hz
     return x.view(1, 1, nx), y.view(1, ny, 1), z.view(nz, 1, 1)
 
 

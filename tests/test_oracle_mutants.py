@@ -31,7 +31,9 @@ MUTANTS = {
                             "double d0 = psi[0], d1 = psi[1], d2 = psi[2]; m = 0.0;"),
     "drops_smallest_axis": ("if (hh[a] != 0.0 && (j < 0 || psi[a] >= psi[j]))",
                             "if (hh[a] != 0.0 && (j < 0 || psi[a] <= psi[j]))"),
-    "h_power": ("hh[a] = 1.0 / m->h;", "hh[a] = 1.0 / (m->h * m->h);"),
+    "h_power": ("hh[a] = 1.0 / m->h3[a];", "hh[a] = 1.0 / (m->h3[a] * m->h3[a]);"),
+    "h_wrong_axis": ("hh[a] = 1.0 / m->h3[a];", "hh[a] = 1.0 / m->h3[0];"),
+    "crossing_wrong_axis": ("double dist = theta * h3[a];", "double dist = theta * h3[0];"),
     "speed_power": ("double Finv2 = 1.0 / (F * F);", "double Finv2 = 1.0 / F;"),
     "crossing_fraction": ("double theta = fc / (fc - fq);",
                           "double theta = fq / (fq - fc);"),
@@ -39,8 +41,10 @@ MUTANTS = {
                           "if (!(fabs(m->T[l]) > Ti))"),
     "adjoint_slowness_factor": ("dLds[p] = lam[p] * sp / D;",
                                 "dLds[p] = lam[p] / (sp * D);"),
-    "adjoint_dropped_weight": ("lam[nbr[q]] += lam[p] * (Tp - fabs(T[nbr[q]])) * w / D;",
-                               "lam[nbr[q]] += lam[p] * w / D;"),
+    "adjoint_dropped_weight": ("lam[nbr[q]] += lam[p] * (Tp - fabs(T[nbr[q]])) * w[ax[q]] / D;",
+                               "lam[nbr[q]] += lam[p] * w[ax[q]] / D;"),
+    "adjoint_weight_wrong_axis": ("D += (Tp - fabs(T[nbr[q]])) * w[ax[q]];",
+                                  "D += (Tp - fabs(T[nbr[q]])) * w[0];"),
     "tangent_sign": ("dT[p] = (sp * v[p] + acc) / D;", "dT[p] = (sp * v[p] - acc) / D;"),
 }
 
@@ -55,6 +59,12 @@ PINS = [
     (pins.test_adjoint_finite_differences, {}),
     (pins.test_adjoint_tangent_dot_product, {}),
     (pins.test_translation_invariance, {}),
+    (pins.test_anisotropic_local_solve, {}),
+    (pins.test_anisotropic_axis_plane_exact, {"axis": 1}),
+    (pins.test_anisotropic_point_source_closed_forms, {}),
+    (pins.test_anisotropic_oblique_plane_front_exact, {}),
+    (pins.test_anisotropic_residual_and_fast_sweep, {"seed": 7, "shape": (9, 13, 7)}),
+    (pins.test_anisotropic_adjoint_finite_differences, {}),
 ]
 
 

@@ -13,6 +13,11 @@ not from re-running the oracle's own formula.
 * first-order convergence to the exact distance (Appendix, Eq. (12))
 * the narrow band stops at width_band (Algorithm 5 / Algorithm 12)
 * adjoint vs central finite differences, adjoint vs tangent (dot product)
+* cells of size dx * dy * dz (Sec. 2.1, Algorithm 11's h_i): per-axis roots
+  against np.roots, axis planes exact with each axis's own cell size, closed
+  forms near a point source, exact front cells of an oblique plane, the
+  weighted residual and weighted fast sweeping, transposing two axes with
+  their cell sizes, the adjoint against finite differences
 """
 import math
 
@@ -430,3 +435,167 @@ def test_wall_with_gap_detours(oracle):
     fin = np.isfinite(T)
     assert np.array_equal(np.isfinite(A), fin)
     assert np.max(np.abs(A[fin] - T[fin])) <= 1e-13 * np.max(T[fin])
+
+
+# --------------------------------------------------------------------------
+# cells of size dx * dy * dz (Sec. 2.1; h_i = 1/dx, 1/dy, 1/dz in Alg. 11)
+# --------------------------------------------------------------------------
+
+H3 = (0.05, 0.08, 0.035)
+
+
+def weighted_root(vals, hs, s):
+    """The unique t with sum_i max(t - v_i, 0)^2 / h_i^2 = s^2 (Eq. (2) with
+    per-axis cell sizes), from np.roots of the k-term quadratic for the
+    sorted values, adding terms while the root exceeds the next value."""
+    pairs = sorted(zip(vals, hs))
+    t = None
+    for k in range(1, len(pairs) + 1):
+        if t is not None and t <= pairs[k - 1][0]:
+            break
+        w = [1.0 / (hh * hh) for _, hh in pairs[:k]]
+        v = [vv for vv, _ in pairs[:k]]
+        a = sum(w)
+        b = -2.0 * sum(wi * vi for wi, vi in zip(w, v))
+        c = sum(wi * vi * vi for wi, vi in zip(w, v)) - s * s
+        t = max(np.roots([a, b, c]).real)
+    return t
+
+
+def eq2_residual_h3(T, h3, F):
+    """eq2_residual with the cell size of each axis."""
+    A = np.abs(T)
+    s = np.zeros_like(A)
+    for ax in range(3):
+        hax = h3[2 - ax]          # numpy axis 0 is z
+        pad = [(0, 0)] * 3
+        pad[ax] = (1, 1)
+        P = np.pad(A, pad, constant_values=np.inf)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -2)
+        hi[ax] = slice(2, None)
+        with np.errstate(invalid="ignore"):
+            term = np.maximum(np.maximum((A - P[tuple(lo)]) / hax, -(P[tuple(hi)] - A) / hax), 0.0)
+        term = np.nan_to_num(term, nan=0.0, posinf=0.0)
+        s += term * term
+    return np.sqrt(s) * F - 1.0
+
+
+def test_anisotropic_local_solve(oracle):
+    inf = np.inf
+    dx, dy, dz = H3
+    # 1-D roots use the cell size of their own axis
+    for a, hh in enumerate(H3):
+        nb = [inf] * 6
+        kn = [0] * 6
+        nb[2 * a + 1] = 0.4
+        kn[2 * a + 1] = 1
+        assert abs(oracle.local_solve(nb, kn, inf, H3, 2.0) - (0.4 + hh / 2.0)) < 1e-15
+    # 2-D and 3-D roots with unequal weights
+    v = oracle.local_solve([1.0, inf, 1.02, inf, inf, inf], [1, 0, 1, 0, 0, 0], inf, H3, 1.0)
+    assert abs(v - weighted_root([1.0, 1.02], [dx, dy], 1.0)) < 1e-14
+    v = oracle.local_solve([1.0, inf, 1.02, inf, 0.99, inf], [1, 0, 1, 0, 1, 0], inf, H3, 1.3)
+    assert abs(v - weighted_root([1.0, 1.02, 0.99], [dx, dy, dz], 1.0 / 1.3)) < 1e-13
+    # a set that is causal with equal cells but not with these: the 1-D root
+    # along the small z cells (0.5 + 0.035) is below the y value 0.54
+    v = oracle.local_solve([inf, inf, 0.54, inf, 0.5, inf], [0, 0, 1, 0, 1, 0], inf, H3, 1.0)
+    assert abs(v - weighted_root([0.54, 0.5], [dy, dz], 1.0)) < 1e-14
+    assert abs(v - (0.5 + dz)) < 1e-15
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_anisotropic_axis_plane_exact(oracle, axis):
+    shape = (9, 11, 13)
+    normal = [0.0, 0.0, 0.0]
+    normal[axis] = 1.0
+    off = 0.43 * shape[2 - axis] * H3[axis]
+    phi = np.broadcast_to(wl.plane_phi0(shape, tuple(normal), off, h=H3), shape).copy()
+    r = oracle.solve_reinit(phi, H3)
+    assert np.max(np.abs(r["T"] - phi)) < 1e-14
+
+
+def test_anisotropic_point_source_closed_forms(oracle):
+    shape = (5, 5, 5)
+    dx, dy, dz = H3
+    r = oracle.solve_sources(shape, [(2, 2, 2)], H3)
+    T = r["T"]
+    for k in range(3):
+        assert abs(T[2, 2, 2 + k] - k * dx) < 1e-15
+        assert abs(T[2, 2 + k, 2] - k * dy) < 1e-15
+        assert abs(T[2 + k, 2, 2] - k * dz) < 1e-15
+    # (i+1, j+1): x neighbour (i, j+1) holds dy, y neighbour (i+1, j) holds dx
+    assert abs(T[2, 3, 3] - weighted_root([dy, dx], [dx, dy], 1.0)) < 1e-15
+    assert abs(T[3, 3, 3] - weighted_root([T[3, 3, 2], T[3, 2, 3], T[2, 3, 3]],
+                                          [dx, dy, dz], 1.0)) < 1e-15
+
+
+def test_anisotropic_oblique_plane_front_exact(oracle):
+    """Plane x + y = c: a front cell whose x and y segments both cross the
+    plane gets the exact distance, since the crossing distances along the
+    axes are |phi| / n_a and (sum_a n_a^2 / phi^2)^(-1/2) = |phi| (Algorithm 8
+    with linear interpolation), whatever the cell sizes."""
+    shape = (6, 20, 24)
+    phi = np.broadcast_to(wl.plane_phi0(shape, (1.0, 1.0, 0.0), 0.62 * math.sqrt(2.0), h=H3),
+                          shape).copy()
+    T, G = oracle.init_reinit(phi, H3)
+    sign = phi >= 0
+    both = G == oracle.KNOWN_FIX
+    for ax in (1, 2):            # numpy axes of y and x
+        cross = np.zeros(shape, bool)
+        for d in (-1, 1):
+            rolled = np.roll(sign, d, ax)
+            edge = [slice(None)] * 3
+            edge[ax] = 0 if d == 1 else -1
+            valid = np.ones(shape, bool)
+            valid[tuple(edge)] = False   # np.roll wraps around
+            cross |= valid & (rolled != sign)
+        both &= cross
+    assert both.sum() > 20
+    assert np.max(np.abs(T[both] - phi[both])) < 1e-14
+
+
+@pytest.mark.parametrize("seed,shape", [(7, (9, 13, 7)), (8, (14, 10, 16))])
+def test_anisotropic_residual_and_fast_sweep(oracle, seed, shape):
+    _, F, src = _rand_problem(seed, shape)
+    r = oracle.solve_sources(shape, src, H3, speed=F, record=True)
+    T, G = r["T"], r["G"]
+    mask = G == oracle.KNOWN_NEW
+    assert np.max(np.abs(eq2_residual_h3(T, H3, F)[mask])) < 1e-10
+    fixed = (G == oracle.KNOWN_FIX).astype(np.uint8)
+    A, rounds = oracle.fast_sweep(np.abs(T) * fixed, fixed, H3, speed=F)
+    assert rounds < 10000
+    assert np.max(np.abs(A - np.abs(T))) <= 1e-13 * np.max(np.abs(T))
+
+
+def test_anisotropic_transposition(oracle):
+    """Swapping the x and y axes together with their cell sizes transposes
+    the solution."""
+    shape = (7, 9, 11)
+    _, F, src = _rand_problem(9, shape)
+    dx, dy, dz = H3
+    a = oracle.solve_sources(shape, src, (dx, dy, dz), speed=F)["T"]
+    src_t = [(j, i, k) for i, j, k in src]
+    b = oracle.solve_sources((7, 11, 9), src_t, (dy, dx, dz),
+                             speed=np.ascontiguousarray(F.transpose(0, 2, 1)))["T"]
+    assert np.max(np.abs(b.transpose(0, 2, 1) - a)) < 1e-15
+
+
+def test_anisotropic_adjoint_finite_differences(oracle):
+    shape = (10, 12, 9)
+    rng = np.random.default_rng(31)
+    modes = wl.draw_fourier_modes(rng)
+    F = wl.fourier_speed(shape, modes, h=H3)
+    src = wl.random_cells(rng, shape, 2)
+    rec = wl.random_cells(rng, shape, 6, exclude=src)
+    s = 1.0 / F
+    L, g, r = _loss_and_grad(oracle, shape, src, rec, H3, s)
+    dLds, _ = oracle.adjoint(r, H3, g, speed=F)
+    for trial in range(3):
+        v = rng.standard_normal(shape)
+        eps = 1e-6 * np.linalg.norm(s) / np.linalg.norm(v)
+        Lp, _, _ = _loss_and_grad(oracle, shape, src, rec, H3, s + eps * v)
+        Lm, _, _ = _loss_and_grad(oracle, shape, src, rec, H3, s - eps * v)
+        fd = (Lp - Lm) / (2 * eps)
+        ad = float(np.sum(dLds * v))
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)

@@ -60,7 +60,8 @@ typedef enum { FMM_TAG_FAR = 0, FMM_TAG_BAND = 1, FMM_TAG_KNOWN = 2, FMM_TAG_FIX
  * other field has a default when left 0. */
 typedef struct {
     int64_t nx, ny, nz;    /* grid size, each >= 1                              */
-    double h;              /* grid spacing (> 0)                                */
+    double h;              /* cell size along x (> 0); also along y and z unless
+                              hy / hz are set                                  */
     int32_t dtype;         /* fmm_dtype                                         */
     int32_t record_tape;   /* 1: keep the upwind sets for fmm_adjoint           */
     double width;          /* width_band (Algorithm 5/12); 0 -> +inf (full march) */
@@ -104,6 +105,12 @@ typedef struct {
                               queued, so the persistent and continuous
                               schedules' waits run into wait_limit_ms (the
                               error path without a fault); 0 normally       */
+    double hy, hz;         /* cell sizes along y and z (Sec. 2.1: cells of
+                              dx * dy * dz, uniform in each direction;
+                              Algorithm 11 uses h_i = 1/dx, 1/dy, 1/dz);
+                              0 -> h.  The stride and the speed term are in
+                              units of h, the bucket width in units of the
+                              smallest cell size.  Batches need 0.          */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */
@@ -203,8 +210,8 @@ fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_
 /*
  * Checkpoints of a solve state, in host memory: the brick-layout psi, tags,
  * tape (when recorded), per-brick BAND minima, halo change masks and dirty
- * flags, and the restart control block, after a 72-byte header that records
- * the grid, dtype, h, record_tape and the kind of speed.
+ * flags, and the restart control block, after an 88-byte header that records
+ * the grid, dtype, cell sizes, record_tape and the kind of speed.
  *   fmm_checkpoint_size -- bytes an image of hd takes (*bytes).
  *   fmm_checkpoint_save -- write the image of the last solve on hd to
  *     host_buf (host memory of at least that size, owned by the caller;
@@ -212,7 +219,7 @@ fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_
  *     limit (fmm_resume's condition); otherwise FMM_ERR_STATE.  Synchronises
  *     hd's stream.
  *   fmm_checkpoint_load -- load an image into hd, which must have been
- *     created with the same grid, dtype, h, record_tape and kind of speed
+ *     created with the same grid, dtype, cell sizes, record_tape and kind of speed
  *     (the speed values themselves, which the image does not hold, must be
  *     the same too); else FMM_ERR_INVALID.  Afterwards hd is as the saving
  *     handle was: fmm_resume continues a stopped solve, fmm_adjoint works on

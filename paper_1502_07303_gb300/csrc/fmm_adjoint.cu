@@ -29,6 +29,7 @@
 #include "fmm_lanes.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace fmmgb {
 namespace {
@@ -111,10 +112,10 @@ __global__ void k_adj_seed(Geom g, Control *ctrl, unsigned *queued, unsigned lon
     }
 }
 
-template <typename real, bool kHetero>
+template <typename real, bool kHetero, bool kAniso>
 __global__ void __launch_bounds__(kAdjWarps * 32)
     k_adj_persistent(Geom g, DeviceState s, const real *__restrict__ dLdT, real *dlds, real *mu_g,
-                     double h, double spd_const_term)
+                     double h, double spd_const_term, double wy, double wz)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -234,16 +235,32 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                     // of the cells still waiting would be thrown away)
                     real lam = (real)0, dsum = (real)0;
                     const real Tp = W.T[ti];
+                    // unequal cells: the terms of axis a carry
+                    // w_a = (h / h_a)^2 (Eq. (2) with h_i per axis)
+                    const real wax[3] = {(real)1, (real)wy, (real)wz};
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int qm = ti - off[a], qp = ti + off[a];
-                        if (tape_axis(W.tp[qm], a) == 2)
-                            lam += W.mu[qm] * (W.T[qm] - Tp);
-                        if (tape_axis(W.tp[qp], a) == 1)
-                            lam += W.mu[qp] * (W.T[qp] - Tp);
+                        const real wa = (kAniso && a > 0) ? wax[a] : (real)1;
+                        if (tape_axis(W.tp[qm], a) == 2) {
+                            if constexpr (kAniso)
+                                lam += wa * (W.mu[qm] * (W.T[qm] - Tp));
+                            else
+                                lam += W.mu[qm] * (W.T[qm] - Tp);
+                        }
+                        if (tape_axis(W.tp[qp], a) == 1) {
+                            if constexpr (kAniso)
+                                lam += wa * (W.mu[qp] * (W.T[qp] - Tp));
+                            else
+                                lam += W.mu[qp] * (W.T[qp] - Tp);
+                        }
                         const int code = tape_axis(W.tp[ti], a);
-                        if (code)
-                            dsum += Tp - W.T[code == 1 ? qm : qp];
+                        if (code) {
+                            if constexpr (kAniso)
+                                dsum += wa * (Tp - W.T[code == 1 ? qm : qp]);
+                            else
+                                dsum += Tp - W.T[code == 1 ? qm : qp];
+                        }
                     }
                     const int c = lane + 32 * k;
                     const int cx = lx, cy = lr + 4 * (k & 1), cz = k >> 1;
@@ -340,20 +357,21 @@ cudaError_t adj_persistent_launch(const Geom &g, const DeviceState &s, const Adj
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const bool het = s.spd != nullptr;
-    if (het)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<real, true>,
+    auto go = [&](auto H, auto A) {
+        constexpr bool het = decltype(H)::value, an = decltype(A)::value;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<real, het, an>,
                                                       kAdjWarps * 32, sm);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<real, false>,
-                                                      kAdjWarps * 32, sm);
-    const int ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        const int ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        k_adj_persistent<real, het, an><<<ctas, kAdjWarps * 32, sm, st>>>(
+            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, a.wy, a.wz);
+    };
+    using Y = std::true_type;
+    using N = std::false_type;
+    const bool het = s.spd != nullptr, an = a.aniso != 0;
     if (het)
-        k_adj_persistent<real, true><<<ctas, kAdjWarps * 32, sm, st>>>(
-            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term);
+        an ? go(Y{}, Y{}) : go(Y{}, N{});
     else
-        k_adj_persistent<real, false><<<ctas, kAdjWarps * 32, sm, st>>>(
-            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term);
+        an ? go(N{}, Y{}) : go(N{}, N{});
     return cudaGetLastError();
 }
 
@@ -361,8 +379,11 @@ template <typename real>
 void adj_configure()
 {
     const int sm = (int)adj_smem<real>();
-    cudaFuncSetAttribute(k_adj_persistent<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_persistent<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaFuncSetAttribute(k_adj_persistent<real, true, false>, attr, sm);
+    cudaFuncSetAttribute(k_adj_persistent<real, false, false>, attr, sm);
+    cudaFuncSetAttribute(k_adj_persistent<real, true, true>, attr, sm);
+    cudaFuncSetAttribute(k_adj_persistent<real, false, true>, attr, sm);
 }
 
 int grid_cap(long long n, int threads, int cap)

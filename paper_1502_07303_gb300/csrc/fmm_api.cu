@@ -132,7 +132,8 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
     }
     hd->speed_const = speed ? 1.0 : speed_const;
     FMM_CUDA(hd, launch_reset_control(s, hd->stream, hd->params.wait_ns, hd->params.hold));
-    FMM_CUDA(hd, launch_load_speed(hd->cfg.dtype, hd->geom, s, hd->params.h, speed,
+    FMM_CUDA(hd, launch_load_speed(hd->cfg.dtype, hd->geom, s, hd->params.h,
+                                   min_spacing(hd->params), speed,
                                    hd->speed_const, hd->stream));
     FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost,
                                  hd->stream));
@@ -313,7 +314,7 @@ struct CkptHeader {
     int32_t version;
     int32_t dtype;
     int64_t nx, ny, nz;
-    double h;
+    double h, hy, hz;
     int32_t record_tape;
     int32_t hetero;
     int32_t resumable;
@@ -321,7 +322,7 @@ struct CkptHeader {
     int64_t bytes;
 };
 constexpr char kCkptMagic[8] = {'F', 'M', 'M', 'C', 'K', 'P', 'T', '1'};
-static_assert(sizeof(CkptHeader) == 72, "the header size fmm.h documents");
+static_assert(sizeof(CkptHeader) == 88, "the header size fmm.h documents");
 
 struct CkptSection {
     void *dev;
@@ -385,6 +386,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return fail(nullptr, FMM_ERR_INVALID, "grid sizes must be in [1, 2^20]");
     if (!(cfg->h > 0.0) || !std::isfinite(cfg->h))
         return fail(nullptr, FMM_ERR_INVALID, "h must be finite and > 0");
+    if (!(cfg->hy >= 0.0) || !std::isfinite(cfg->hy) || !(cfg->hz >= 0.0) || !std::isfinite(cfg->hz))
+        return fail(nullptr, FMM_ERR_INVALID, "hy and hz must be finite and >= 0 (0 -> h)");
     if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
         return fail(nullptr, FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
@@ -420,9 +423,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     g.nbz = (g.nz + kB - 1) / kB;
     g.nbricks = (long long)g.nbx * g.nby * g.nbz;
     SolveParams &p = hd->params;
-    p.h = cfg->h;
-    const double hh = 1.0 / cfg->h;
-    p.w = hh * hh;
+    set_spacing(p, cfg->h, cfg->hy, cfg->hz);
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
     const double stride_h = cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype);
     p.stride = stride_h * cfg->h;
@@ -554,6 +555,9 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     a.mu = hd->adj_mu;
     a.h = hd->params.h;
     a.spd_term = hd->params.spd_term;
+    a.wy = hd->params.wy;
+    a.wz = hd->params.wz;
+    a.aniso = hd->params.aniso;
     // every cell becomes ready once its downwind neighbours have published;
     // one persistent launch processes bricks until none is queued
     hd->resumable = false;   // the adjoint reuses the control block and the flags
@@ -642,6 +646,8 @@ fmm_status fmm_checkpoint_save(fmm_handle *hd, void *host_buf, int64_t capacity)
     hdr.ny = hd->geom.ny;
     hdr.nz = hd->geom.nz;
     hdr.h = hd->params.h;
+    hdr.hy = hd->params.hy;
+    hdr.hz = hd->params.hz;
     hdr.record_tape = hd->st.tape != nullptr;
     hdr.hetero = hd->st.spd != nullptr;
     hdr.resumable = hd->resumable;
@@ -671,7 +677,8 @@ fmm_status fmm_checkpoint_load(fmm_handle *hd, const void *host_buf, int64_t siz
     if (memcmp(hdr.magic, kCkptMagic, sizeof(hdr.magic)) != 0 || hdr.version != 1)
         return fail(hd, FMM_ERR_INVALID, "not a checkpoint of this library");
     if (hdr.dtype != hd->cfg.dtype || hdr.nx != hd->geom.nx || hdr.ny != hd->geom.ny ||
-        hdr.nz != hd->geom.nz || hdr.h != hd->params.h)
+        hdr.nz != hd->geom.nz || hdr.h != hd->params.h || hdr.hy != hd->params.hy ||
+        hdr.hz != hd->params.hz)
         return fail(hd, FMM_ERR_INVALID, "checkpoint grid or dtype differs from the handle's");
     if ((hdr.record_tape != 0) != (hd->st.tape != nullptr) || (hdr.hetero != 0) != (hd->st.spd != nullptr))
         return fail(hd, FMM_ERR_INVALID, "checkpoint record_tape or speed kind differs from the handle's");
@@ -717,6 +724,8 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
         return fail(nullptr, FMM_ERR_INVALID, "bad width, stride, bucket or exchange_passes");
     if (cfg->record_tape)
         return fail(nullptr, FMM_ERR_INVALID, "batches keep no tape (record_tape must be 0)");
+    if (cfg->hy != 0.0 || cfg->hz != 0.0)
+        return fail(nullptr, FMM_ERR_INVALID, "batches use cubic cells (hy and hz must be 0)");
     std::vector<BatchGrid> grids((size_t)n_grids);
     long long total = 0;
     double hmin = INFINITY;
@@ -776,8 +785,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     memset(&g, 0, sizeof(g));
     g.nbricks = total;
     SolveParams &p = hd->params;
-    p.h = hmin;
-    p.w = (1.0 / hmin) * (1.0 / hmin);
+    set_spacing(p, hmin, 0.0, 0.0);
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * hmin;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;

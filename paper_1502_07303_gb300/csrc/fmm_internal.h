@@ -86,8 +86,9 @@ struct Geom {
 
 // Parameters of one solve.
 struct SolveParams {
-    double h;
-    double w;           // (1/h)^2, the h_i^2 of Algorithm 11
+    double h;           // cell size along x; the stride and the speed term
+                        // (h/F)^2 are in its units
+    double w;           // (1/h)^2
     double width;       // width_band
     double stride;      // delta_s (absolute units)
     double bucket;      // bucket width factor
@@ -101,7 +102,29 @@ struct SolveParams {
     double max_lead;    // continuous schedule: lead of the bound in strides
     unsigned long long wait_ns;   // limit of a device wait without progress
     int hold;           // testing: keep one phantom brick pending
+    int aniso;          // hy or hz differs from h
+    double hy, hz;      // cell sizes along y and z (h on a cubic-cell grid)
+    double wy, wz;      // (h/hy)^2, (h/hz)^2: the h_i^2 of Algorithm 11
+                        // relative to the x axis
 };
+
+// Cell sizes of Sec. 2.1 (hy, hz <= 0 mean h) and the per-axis weights of
+// Algorithm 11 relative to the x axis.
+inline void set_spacing(SolveParams &p, double h, double hy, double hz)
+{
+    p.h = h;
+    p.hy = hy > 0.0 ? hy : h;
+    p.hz = hz > 0.0 ? hz : h;
+    p.wy = (h / p.hy) * (h / p.hy);
+    p.wz = (h / p.hz) * (h / p.hz);
+    p.aniso = p.hy != h || p.hz != h;
+    p.w = (1.0 / h) * (1.0 / h);
+}
+inline double min_spacing(const SolveParams &p)
+{
+    const double m = p.h < p.hy ? p.h : p.hy;
+    return m < p.hz ? m : p.hz;
+}
 
 constexpr int kSchedulePhased = 1;
 constexpr int kSchedulePersistent = 2;
@@ -164,8 +187,10 @@ cudaError_t launch_init_sources(int dtype, const Geom &g, const DeviceState &s,
 cudaError_t launch_init_reinit(int dtype, const Geom &g, const DeviceState &s,
                                const SolveParams &p, const void *phi0,
                                cudaStream_t stream);
+// h: the x cell size of the speed term (h/F)^2; hmin: the smallest cell size,
+// the unit of the bucket width
 cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s,
-                              double h, const void *speed, double speed_const,
+                              double h, double hmin, const void *speed, double speed_const,
                               cudaStream_t stream);
 cudaError_t launch_front_init(int dtype, const Geom &g, const DeviceState &s,
                               const SolveParams &p, cudaStream_t stream);
@@ -207,6 +232,8 @@ struct AdjointArgs {
     void *mu;           // lambda / D per cell (brick layout), NaN until done
     double h;
     double spd_term;    // (h/F)^2 of a constant speed
+    double wy, wz;      // (h/hy)^2, (h/hz)^2 (1 on a cubic-cell grid)
+    int aniso;
 };
 cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
                                 const AdjointArgs &a, cudaStream_t stream);

@@ -213,6 +213,89 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
     return INF;
 }
 
+// Algorithm 11 with cells of size h * hy * hz: h_i^2 (t - psi_i)^2 summed
+// over the set equals F^-2, i.e. sum_i w_i (u - delta_i)^2 = q with
+// w_i = (h / h_i)^2 (w_x = 1), q = (h/F)^2 and the same shift t = m + u.
+// The per-axis values are sorted together with their weights (and sides);
+// with K = sum w_i, S = sum w_i delta_i and Q = sum w_i delta_i^2 over the
+// set, disc = S^2 - K (Q - q) and u = (S + sqrt(disc)) / K; the largest
+// remaining value is dropped while the set is not causal, as above.
+template <typename real>
+__device__ __forceinline__ void cswap_w(real &a, real &wa, unsigned &ca, real &b, real &wb, unsigned &cb)
+{
+    if (lt(b, a)) {
+        const real t = a, tw = wa;
+        a = b;
+        b = t;
+        wa = wb;
+        wb = tw;
+        const unsigned c = ca;
+        ca = cb;
+        cb = c;
+    }
+}
+__device__ __forceinline__ float vdiv(float a, float b) { return a / b; }
+__device__ __forceinline__ double vdiv(double a, double b) { return div_fp64(a, b); }
+
+template <typename real>
+__device__ __forceinline__ real solve_cell_w(const real *kv, int ti, real Tc, real q, real wy,
+                                             real wz, uint8_t &set_out)
+{
+    const int off[3] = {1, kTile, kTile * kTile};
+    const real wax[3] = {(real)1, wy, wz};
+    const real INF = inf_v<real>();
+    real v[3], w[3];
+    unsigned code[3];
+    int nd = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
+        const real mn = vmin(vm, vp);
+        const bool up = lt(mn, Tc);
+        v[a] = up ? mn : INF;
+        w[a] = up ? wax[a] : (real)0;
+        code[a] = up ? (lt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
+        nd += up;
+    }
+    set_out = 0;
+    if (nd == 0)
+        return INF;
+    // stable sort of three, each weight and side with its value
+    cswap_w(v[0], w[0], code[0], v[1], w[1], code[1]);
+    cswap_w(v[1], w[1], code[1], v[2], w[2], code[2]);
+    cswap_w(v[0], w[0], code[0], v[1], w[1], code[1]);
+    const real m = v[0];
+    real d1 = nd >= 2 ? v[1] - m : (real)0;
+    real d2 = nd >= 3 ? v[2] - m : (real)0;
+    const real w0 = w[0];
+    real w1 = nd >= 2 ? w[1] : (real)0;
+    real w2 = nd >= 3 ? w[2] : (real)0;
+#pragma unroll 1
+    for (; nd != 0; --nd) {
+        const real K = w0 + w1 + w2;
+        const real S = fma(w1, d1, w2 * d2);
+        const real Q = fma(w1 * d1, d1, (w2 * d2) * d2);
+        const real disc = fma(-K, Q - q, S * S);
+        if (!lt(disc, (real)0)) {
+            const real u = vdiv(S + vsqrt(disc), K);
+            const real dmax = nd == 3 ? d2 : d1;   // 0 when nd == 1
+            if (lt(dmax, u)) {
+                set_out = (uint8_t)(code[0] | (nd >= 2 ? code[1] : 0u) | (nd == 3 ? code[2] : 0u));
+                return m + u;
+            }
+        }
+        // drop the largest remaining value with its weight
+        if (nd == 3) {
+            d2 = (real)0;
+            w2 = (real)0;
+        } else {
+            d1 = (real)0;
+            w1 = (real)0;
+        }
+    }
+    return INF;
+}
+
 // Warp minimum of non-negative values (or +inf): their bit patterns order
 // like the values, so the integer reductions of the warp do it exactly (a
 // double in two steps, high word then low word).
@@ -279,11 +362,15 @@ __device__ __forceinline__ float crossing(float fc, float fq, double h)
     return (fc / (fc - fq)) * (float)h;
 }
 
-// Algorithm 8 for one cell (i, j, k) of an nx*ny*nz level set.
+// Algorithm 8 for one cell (i, j, k) of an nx*ny*nz level set with cells of
+// size hx * hy * hz (the crossing distance of an axis is a fraction of that
+// axis's cell size).
 template <typename real>
 __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx, int ny, int nz,
-                                            int i, int j, int k, double h, real &Tv, uint8_t &tg)
+                                            int i, int j, int k, double hx, double hy, double hz,
+                                            real &Tv, uint8_t &tg)
 {
+    const double hs[3] = {hx, hy, hz};
     const long long sx = 1, sy = nx, sz = (long long)nx * ny;
     const long long p = (long long)k * sz + (long long)j * sy + i;
     const real fc = phi[p];
@@ -304,7 +391,7 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
             const real fq = phi[p + dir * st[a]];
             if ((fq >= (real)0) == pos)
                 continue;
-            const real dist = crossing(fc, fq, h);
+            const real dist = crossing(fc, fq, hs[a]);
             if (dist < d[a])
                 d[a] = dist;
             any = true;
@@ -331,8 +418,8 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
 }
 
 template <typename real>
-__global__ void k_init_reinit(Geom g, double h, const real *__restrict__ phi, real *T,
-                              uint8_t *tag)
+__global__ void k_init_reinit(Geom g, double hx, double hy, double hz,
+                              const real *__restrict__ phi, real *T, uint8_t *tag)
 {
     const long long n = g.nbricks * kB3;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -348,14 +435,15 @@ __global__ void k_init_reinit(Geom g, double h, const real *__restrict__ phi, re
         }
         real Tv;
         uint8_t tg;
-        reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, h, Tv, tg);
+        reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, hx, hy, hz, Tv, tg);
         T[e] = Tv;
         tag[e] = tg;
     }
 }
 
-// Speed field to brick layout: the speed term (h/F)^2 of the shifted solve.
-// Each brick also records its bucket width h * min(1/F) / sqrt(3).
+// Speed field to brick layout: the speed term (h/F)^2 of the shifted solve
+// (h the x cell size).  Each brick also records its bucket width
+// hmin * min(1/F) / sqrt(3), hmin the smallest cell size.
 __device__ __forceinline__ double speed_term(double F, double h) { return (h * h) / (F * F); }
 __device__ __forceinline__ float speed_term(float F, double h)
 {
@@ -364,7 +452,8 @@ __device__ __forceinline__ float speed_term(float F, double h)
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const real *__restrict__ speed,
+__global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, double hmin,
+                                                         const real *__restrict__ speed,
                                                          double speed_const, real *spd, real *bdelta,
                                                          Control *ctrl)
 {
@@ -399,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, const
                 m = fmax(m, red[w]);
             if (!(m > (real)0))
                 m = (real)speed_const;
-            bdelta[b] = (real)(h / (1.7320508075688772 * (double)m));
+            bdelta[b] = (real)(hmin / (1.7320508075688772 * (double)m));
         }
         __syncthreads();
     }
@@ -474,10 +563,11 @@ struct MarchStats {
 // kFresh: read the brick and halo through L2 (the persistent kernel, where the
 // brick may have been written by another SM during the same launch).  kTape:
 // record the upwind set of every solve for the adjoint (without it the
-// compiler drops the set bookkeeping of Algorithm 11 altogether).  On
+// compiler drops the set bookkeeping of Algorithm 11 altogether).  kAniso:
+// cells of unequal sizes (the weighted solve).  On
 // return, lanes 0..5 hold in notify_m / notify_nb the changed boundary cells
 // and the neighbour brick across face = lane (mode 1).
-template <typename real, bool kHetero, int kMode, bool kFresh, bool kTape>
+template <typename real, bool kHetero, int kMode, bool kFresh, bool kTape, bool kAniso>
 __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s, const SolveParams &p,
                                             double spd_const_term, WarpTile<real> &W, long long b,
                                             const unsigned long long *F_in, real bound0, real bound1,
@@ -613,7 +703,10 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
                 ti = tile_of(c);
                 tc = W.tv[c];
                 const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
-                cand = solve_cell<real, kTape>(W.kv, ti, tc, sp, cset);
+                if constexpr (kAniso)
+                    cand = solve_cell_w<real>(W.kv, ti, tc, sp, (real)p.wy, (real)p.wz, cset);
+                else
+                    cand = solve_cell<real, kTape>(W.kv, ti, tc, sp, cset);
             }
             __syncwarp();
             // each cell appears once in the list, so tc is still its value
@@ -800,7 +893,7 @@ __device__ __forceinline__ void flush_stats(Control *ctrl, MarchStats &st, int l
 // Algorithm 12 over the bricks of work list `which` (taken one at a time from
 // a shared counter) with the change masks the select kernel moved to the
 // inbox; changes are flagged in the neighbours' live masks and dirty flags.
-template <typename real, bool kHetero, int kMode, bool kTape>
+template <typename real, bool kHetero, int kMode, bool kTape, bool kAniso>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
 {
@@ -835,7 +928,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = kMode == 1 ? s.inbox[b * kFaces + f] : 0ull;
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, kMode, false, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, kMode, false, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                                  lane, m, nb, st);
         if (kMode == 1 && m) {
             atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
@@ -869,7 +962,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // past the limit the kernel sets ERR_SPIN and returns.
 // ---------------------------------------------------------------------------
 
-template <typename real, bool kHetero, bool kTape>
+template <typename real, bool kHetero, bool kTape, bool kAniso>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
@@ -901,7 +994,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, 1, true, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, 1, true, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                             lane, m, nb, st);
         // publish the write-back before flagging anything
         __threadfence();
@@ -1173,7 +1266,7 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
     job = 2;
 }
 
-template <typename real, bool kHetero, bool kTape>
+template <typename real, bool kHetero, bool kTape, bool kAniso>
 __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     k_march_continuous(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
@@ -1227,7 +1320,7 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
-        march_brick<real, kHetero, 1, true, kTape>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
+        march_brick<real, kHetero, 1, true, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
                                             lane, m, nb, st);
         __threadfence();
         __syncwarp();
@@ -1530,7 +1623,7 @@ __global__ void k_batch_init_reinit(const BatchGrid *__restrict__ grids, const i
         }
         real Tv;
         uint8_t tg;
-        reinit_cell<real>((const real *)G.phi0, G.nx, G.ny, G.nz, i, j, k, G.h, Tv, tg);
+        reinit_cell<real>((const real *)G.phi0, G.nx, G.ny, G.nz, i, j, k, G.h, G.h, G.h, Tv, tg);
         T[e] = Tv;
         tag[e] = tg;
     }
@@ -1618,22 +1711,29 @@ __global__ void k_reset_list(Control *c, int which)
     c->work[which] = 0u;
 }
 
-// Calls f with the speed-field and tape flags as compile-time constants
-// (std::true_type / std::false_type), one kernel instantiation per pair.
+// Calls f with the speed-field, tape and unequal-cell flags as compile-time
+// constants (std::true_type / std::false_type), one kernel instantiation per
+// combination.
 template <typename Fn>
-void with_flags(bool het, bool tape, Fn &&f)
+void with_flags(bool het, bool tape, bool aniso, Fn &&f)
 {
     using Y = std::true_type;
     using N = std::false_type;
+    auto third = [&](auto H, auto P) {
+        if (aniso)
+            f(H, P, Y{});
+        else
+            f(H, P, N{});
+    };
     if (het) {
         if (tape)
-            f(Y{}, Y{});
+            third(Y{}, Y{});
         else
-            f(Y{}, N{});
+            third(Y{}, N{});
     } else if (tape) {
-        f(N{}, Y{});
+        third(N{}, Y{});
     } else {
-        f(N{}, N{});
+        third(N{}, N{});
     }
 }
 
@@ -1653,12 +1753,12 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             k_trace_seed<<<1, 1, 0, st>>>(s.ctrl, trace);
         if (ev)
             cudaEventRecord(ev[0], st);
-        with_flags(het, tape, [&](auto H, auto P) {
-            constexpr bool h = decltype(H)::value, t = decltype(P)::value;
+        with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
+            constexpr bool h = decltype(H)::value, t = decltype(P)::value, an = decltype(A)::value;
             if (p.schedule == kScheduleContinuous)
-                k_march_continuous<real, h, t><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+                k_march_continuous<real, h, t, an><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
             else
-                k_march_persistent<real, h, t><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
+                k_march_persistent<real, h, t, an><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
         });
         if (ev)
             cudaEventRecord(ev[1], st);
@@ -1674,8 +1774,8 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             k_trace<<<1, 1, 0, st>>>(s.ctrl, which, pass, trace + 3 * pass);
         if (ev)
             cudaEventRecord(ev[2 * pass], st);
-        with_flags(het, tape, [&](auto H, auto P) {
-            k_march<real, decltype(H)::value, 1, decltype(P)::value>
+        with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
+            k_march<real, decltype(H)::value, 1, decltype(P)::value, decltype(A)::value>
                 <<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
         });
         if (ev)
@@ -1691,8 +1791,8 @@ cudaError_t front_init_impl(const Geom &g, const DeviceState &s, const SolvePara
     const long long need = (g.nbricks + kMarchWarps - 1) / kMarchWarps;
     const int nb = (int)(need < s.march_ctas ? need : s.march_ctas);
     const size_t sm = march_smem<real>();
-    with_flags(s.spd != nullptr, s.tape != nullptr, [&](auto H, auto P) {
-        k_march<real, decltype(H)::value, 0, decltype(P)::value>
+    with_flags(s.spd != nullptr, s.tape != nullptr, p.aniso != 0, [&](auto H, auto P, auto A) {
+        k_march<real, decltype(H)::value, 0, decltype(P)::value, decltype(A)::value>
             <<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
     });
     return cudaGetLastError();
@@ -1703,17 +1803,17 @@ int configure_march()
 {
     const int sm = (int)march_smem<real>();
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    for (int h = 0; h < 2; ++h)
-        for (int t = 0; t < 2; ++t)
-            with_flags(h != 0, t != 0, [&](auto H, auto P) {
-                constexpr bool hh = decltype(H)::value, tt = decltype(P)::value;
-                cudaFuncSetAttribute(k_march<real, hh, 1, tt>, attr, sm);
-                cudaFuncSetAttribute(k_march<real, hh, 0, tt>, attr, sm);
-                cudaFuncSetAttribute(k_march_persistent<real, hh, tt>, attr, sm);
-                cudaFuncSetAttribute(k_march_continuous<real, hh, tt>, attr, sm);
-            });
+    for (int f = 0; f < 8; ++f)
+        with_flags((f & 1) != 0, (f & 2) != 0, (f & 4) != 0, [&](auto H, auto P, auto A) {
+            constexpr bool hh = decltype(H)::value, tt = decltype(P)::value, an = decltype(A)::value;
+            cudaFuncSetAttribute(k_march<real, hh, 1, tt, an>, attr, sm);
+            cudaFuncSetAttribute(k_march<real, hh, 0, tt, an>, attr, sm);
+            cudaFuncSetAttribute(k_march_persistent<real, hh, tt, an>, attr, sm);
+            cudaFuncSetAttribute(k_march_continuous<real, hh, tt, an>, attr, sm);
+        });
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1, true>, kMarchWarps * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1, true, false>, kMarchWarps * 32,
+                                                  sm);
     return n > 0 ? n : 1;
 }
 
@@ -1746,21 +1846,23 @@ cudaError_t launch_init_reinit(int dtype, const Geom &g, const DeviceState &s,
 {
     const int nb = grid_for(g.nbricks * kB3, 256, 152 * 32);
     if (dtype == 1)
-        k_init_reinit<double><<<nb, 256, 0, st>>>(g, p.h, (const double *)phi0, (double *)s.T, s.tag);
+        k_init_reinit<double><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const double *)phi0,
+                                                  (double *)s.T, s.tag);
     else
-        k_init_reinit<float><<<nb, 256, 0, st>>>(g, p.h, (const float *)phi0, (float *)s.T, s.tag);
+        k_init_reinit<float><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const float *)phi0,
+                                                 (float *)s.T, s.tag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s, double h,
-                              const void *speed, double speed_const, cudaStream_t st)
+                              double hmin, const void *speed, double speed_const, cudaStream_t st)
 {
     const int nb = grid_for(g.nbricks, 1, 152 * 8);
     if (dtype == 1)
-        k_load_speed<double><<<nb, kThreads, 0, st>>>(g, h, (const double *)speed, speed_const,
+        k_load_speed<double><<<nb, kThreads, 0, st>>>(g, h, hmin, (const double *)speed, speed_const,
                                                       (double *)s.spd, (double *)s.bdelta, s.ctrl);
     else
-        k_load_speed<float><<<nb, kThreads, 0, st>>>(g, h, (const float *)speed, speed_const,
+        k_load_speed<float><<<nb, kThreads, 0, st>>>(g, h, hmin, (const float *)speed, speed_const,
                                                      (float *)s.spd, (float *)s.bdelta, s.ctrl);
     return cudaGetLastError();
 }

@@ -104,6 +104,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
         return error(FMM_ERR_INVALID, "grid sizes must be in [1, 2^20]");
     if (!(cfg->h > 0.0) || !std::isfinite(cfg->h))
         return error(FMM_ERR_INVALID, "h must be finite and > 0");
+    if (!(cfg->hy >= 0.0) || !std::isfinite(cfg->hy) || !(cfg->hz >= 0.0) || !std::isfinite(cfg->hz))
+        return error(FMM_ERR_INVALID, "hy and hz must be finite and >= 0 (0 -> h)");
     if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
         return error(FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
@@ -159,9 +161,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
 
     SolveParams p;
     memset(&p, 0, sizeof(p));
-    p.h = cfg->h;
-    const double hh = 1.0 / cfg->h;
-    p.w = hh * hh;
+    set_spacing(p, cfg->h, cfg->hy, cfg->hz);
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
@@ -198,7 +198,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     NA_CUDA(cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     NA_CUDA(cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
     NA_CUDA(cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
-    NA_CUDA(launch_load_speed(dt, g, s, p.h, nullptr, 1.0, st));
+    NA_CUDA(launch_load_speed(dt, g, s, p.h, min_spacing(p), nullptr, 1.0, st));
     NA_CUDA(launch_init_reinit(dt, g, s, p, phi0, st));
     NA_CUDA(launch_front_init(dt, g, s, p, st));
     // the loop of Algorithm 16; the control block is read back into a

@@ -22,7 +22,8 @@ TAG_FAR, TAG_BAND, TAG_KNOWN, TAG_FIX = 0, 1, 2, 3
 EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
             "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch",
-            "fmm_get_trace")
+            "fmm_get_trace", "fmm_resume", "fmm_checkpoint_size", "fmm_checkpoint_save",
+            "fmm_checkpoint_load")
 
 
 class FmmConfig(ctypes.Structure):
@@ -34,7 +35,8 @@ class FmmConfig(ctypes.Structure):
                 ("max_restarts", ctypes.c_int64), ("stream", ctypes.c_void_p),
                 ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32),
-                ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32)]
+                ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32),
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
 
 
 class FmmStats(ctypes.Structure):
@@ -133,10 +135,19 @@ def _dev_ptr(t: torch.Tensor, dtype=None, shape=None, name="array"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _spacing(h):
+    """(dx, dy, dz) from one cell size or a 3-sequence."""
+    if isinstance(h, (int, float)):
+        return float(h), float(h), float(h)
+    hx, hy, hz = (float(v) for v in h)
+    return hx, hy, hz
+
+
 class Solver:
-    """One handle of the CUDA library: a grid (nz, ny, nx), spacing h, dtype,
-    a speed field (tensor on the device or a constant) and optional point
-    sources (i, j, k)."""
+    """One handle of the CUDA library: a grid (nz, ny, nx), cell size h (one
+    value, or (dx, dy, dz) for cells of unequal sides), dtype, a speed field
+    (tensor on the device or a constant) and optional point sources
+    (i, j, k)."""
 
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
@@ -149,7 +160,8 @@ class Solver:
         self.stream = stream
         cfg = FmmConfig()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
-        cfg.h = float(h)
+        hx, hy, hz = _spacing(h)
+        cfg.h, cfg.hy, cfg.hz = hx, hy, hz
         cfg.dtype = self.code
         cfg.record_tape = 1 if record_tape else 0
         cfg.width = 0.0 if math.isinf(width) else float(width)
@@ -179,7 +191,7 @@ class Solver:
         if rc != FMM_OK:
             raise FmmError(rc, self.lib.fmm_last_error(None).decode())
         self.handle = handle
-        self.h = float(h)
+        self.h = hx if (hy, hz) == (hx, hx) else (hx, hy, hz)
 
     def _speed_args(self, speed):
         if speed is None:
@@ -390,7 +402,7 @@ def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=0.0, bu
     nz, ny, nx = phi0.shape
     cfg = FmmConfig()
     cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
-    cfg.h = float(h)
+    cfg.h, cfg.hy, cfg.hz = _spacing(h)
     cfg.dtype = code
     cfg.width = 0.0 if math.isinf(width) else float(width)
     cfg.stride = float(stride)

@@ -15,12 +15,18 @@
  *
  * Conventions shared by every entry point
  *   - Grid arrays are nx*ny*nz elements, x fastest: idx = (k*ny + j)*nx + i,
- *     psi at cell centres, spacing h on every axis (Sec. 2.1).  Cells outside
+ *     psi at cell centres of cells h * hy * hz (Sec. 2.1).  Cells outside
  *     the grid do not exist; stencils never leave it (Sec. 4.1).
- *   - Array arguments marked "device" are caller-owned device memory on the
- *     current CUDA device, contiguous, 16-byte aligned, of the handle's dtype
- *     (float for FMM_F32, double for FMM_F64) unless stated otherwise.  The
- *     library never frees them and keeps no reference after the call returns.
+ *   - Array arguments marked "device" are caller-owned memory, contiguous,
+ *     16-byte aligned, of the handle's dtype (float for FMM_F32, double for
+ *     FMM_F64) unless stated otherwise: device (or managed) memory of the
+ *     current CUDA device, or -- for fmm_create / fmm_set_speed's speed,
+ *     fmm_solve, fmm_reinit_signed_distance, fmm_resume and fmm_adjoint --
+ *     host memory, page-locked or pageable.  Host arrays are copied through
+ *     device buffers the handle owns (allocated on first use, freed by
+ *     fmm_destroy) on cfg->stream, inputs before the solve and outputs after
+ *     it, and the call returns once host outputs are written.  The library
+ *     never frees caller arrays and keeps no reference after the call returns.
  *   - Work is enqueued on cfg->stream (NULL = the legacy default stream).
  *     Entry points that run a solve return after it has finished (the restart
  *     loop reads the device's termination flag), so outputs are ready when

@@ -37,6 +37,10 @@ struct fmm_handle {
     std::vector<fmm_trace_entry> trace;
     void *adj_mu = nullptr;            // adjoint workspace (lambda / D per cell)
     unsigned *adj_count = nullptr;
+    // device copies of the caller's host arrays (x-fastest, allocated on
+    // first use): inputs and psi / dL/ds, a second array, tags
+    void *stage[2] = {nullptr, nullptr};
+    uint8_t *stage_tags = nullptr;
     // batches (fmm_create_batch)
     int n_grids = 0;
     BatchGrid *d_grids = nullptr;
@@ -107,6 +111,14 @@ void free_state(fmm_handle *hd)
         cudaFree(hd->adj_count);
     hd->adj_mu = nullptr;
     hd->adj_count = nullptr;
+    for (void *&p : hd->stage) {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+    }
+    if (hd->stage_tags)
+        cudaFree(hd->stage_tags);
+    hd->stage_tags = nullptr;
     memset(&hd->st, 0, sizeof(hd->st));
     hd->d_src = nullptr;
     hd->h_ctrl = nullptr;
@@ -116,6 +128,52 @@ template <typename T>
 cudaError_t alloc(T **p, size_t bytes)
 {
     return cudaMalloc((void **)p, bytes < 16 ? 16 : bytes);
+}
+
+// A caller's array in host memory (page-locked or pageable) rather than in
+// device memory (managed memory counts as device memory).
+bool is_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error of an unknown pointer
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// The grid's cells in the caller's x-fastest layout.
+size_t natural_cells(const fmm_handle *hd)
+{
+    return (size_t)hd->geom.nx * hd->geom.ny * hd->geom.nz;
+}
+
+// Device buffer k of the host staging (n values of the dtype), allocated on
+// first use.
+fmm_status stage_buffer(fmm_handle *hd, int k, void **out)
+{
+    if (!hd->stage[k])
+        FMM_CUDA(hd, alloc(&hd->stage[k], natural_cells(hd) * hd->rsize));
+    *out = hd->stage[k];
+    return FMM_OK;
+}
+
+// An input array as the kernels read it: host arrays are copied (on the
+// handle's stream) into staging buffer k.
+fmm_status device_input(fmm_handle *hd, const void *arr, int k, const void **out)
+{
+    if (!is_host(arr)) {
+        *out = arr;
+        return FMM_OK;
+    }
+    void *buf = nullptr;
+    const fmm_status r = stage_buffer(hd, k, &buf);
+    if (r != FMM_OK)
+        return r;
+    FMM_CUDA(hd, cudaMemcpyAsync(buf, arr, natural_cells(hd) * hd->rsize, cudaMemcpyHostToDevice,
+                                 hd->stream));
+    *out = buf;
+    return FMM_OK;
 }
 
 fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
@@ -131,6 +189,11 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
         s.spd = nullptr;
     }
     hd->speed_const = speed ? 1.0 : speed_const;
+    if (speed) {
+        const fmm_status r = device_input(hd, speed, 0, &speed);
+        if (r != FMM_OK)
+            return r;
+    }
     FMM_CUDA(hd, launch_reset_control(s, hd->stream, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, launch_load_speed(hd->cfg.dtype, hd->geom, s, hd->params.h,
                                    min_spacing(hd->params), speed,
@@ -249,8 +312,28 @@ fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long lon
     hd->stats.n_bricks = g.nbricks;
     hd->stats.error_flags = c.error;
     if (T_out) {
-        FMM_CUDA(hd, launch_output(dt, g, s, T_out, tags_out, st));
+        // host outputs go through the staging buffers (the input the first
+        // one held was consumed by the initialisation, earlier on the stream)
+        const bool host_T = is_host(T_out), host_G = tags_out && is_host(tags_out);
+        void *Td = T_out;
+        uint8_t *Gd = tags_out;
+        if (host_T) {
+            const fmm_status r = stage_buffer(hd, 0, &Td);
+            if (r != FMM_OK)
+                return r;
+        }
+        if (host_G) {
+            if (!hd->stage_tags)
+                FMM_CUDA(hd, alloc(&hd->stage_tags, natural_cells(hd)));
+            Gd = hd->stage_tags;
+        }
+        FMM_CUDA(hd, launch_output(dt, g, s, Td, Gd, st));
         launches += 1;
+        if (host_T)
+            FMM_CUDA(hd, cudaMemcpyAsync(T_out, Td, natural_cells(hd) * hd->rsize,
+                                         cudaMemcpyDeviceToHost, st));
+        if (host_G)
+            FMM_CUDA(hd, cudaMemcpyAsync(tags_out, Gd, natural_cells(hd), cudaMemcpyDeviceToHost, st));
     }
     FMM_CUDA(hd, cudaStreamSynchronize(st));
     // restarts after the terminating pass only return; the march launches
@@ -507,7 +590,7 @@ fmm_status fmm_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     if (!hd)
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (!T_out || !aligned16(T_out))
-        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned pointer");
     if (hd->n_grids)
         return fail(hd, FMM_ERR_STATE, "a batch handle solves with fmm_reinit_batch");
     FMM_CUDA(hd, launch_init_sources(hd->cfg.dtype, hd->geom, hd->st, hd->d_src, hd->n_src, hd->stream));
@@ -521,11 +604,14 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
     if (!hd)
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (!phi0 || !aligned16(phi0))
-        return fail(hd, FMM_ERR_INVALID, "phi0 must be a 16-byte aligned device pointer");
+        return fail(hd, FMM_ERR_INVALID, "phi0 must be a 16-byte aligned pointer");
     if (!T_out || !aligned16(T_out))
-        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned pointer");
     if (hd->n_grids)
         return fail(hd, FMM_ERR_STATE, "a batch handle solves with fmm_reinit_batch");
+    const fmm_status r = device_input(hd, phi0, 0, &phi0);
+    if (r != FMM_OK)
+        return r;
     FMM_CUDA(hd, launch_init_reinit(hd->cfg.dtype, hd->geom, hd->st, hd->params, phi0, hd->stream));
     hd->pre_launches = 1;
     return run_solve(hd, T_out, tags_out);
@@ -536,7 +622,7 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     if (!hd)
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (!dL_dT || !dL_dslowness)
-        return fail(hd, FMM_ERR_INVALID, "dL_dT and dL_dslowness must be device pointers");
+        return fail(hd, FMM_ERR_INVALID, "dL_dT and dL_dslowness must not be NULL");
     if (!hd->solved || !hd->tape_valid)
         return fail(hd, FMM_ERR_STATE, "fmm_adjoint needs a solve with record_tape = 1 first");
     if (!aligned16(dL_dT) || !aligned16(dL_dslowness))
@@ -549,9 +635,16 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
         FMM_CUDA(hd, alloc(&hd->adj_mu, (size_t)g.nbricks * kB3 * hd->rsize));
     if (!hd->adj_count)
         FMM_CUDA(hd, alloc(&hd->adj_count, sizeof(unsigned)));
+    const bool host_out = is_host(dL_dslowness);
+    fmm_status r = device_input(hd, dL_dT, 0, &dL_dT);
+    void *dlds = dL_dslowness;
+    if (r == FMM_OK && host_out)
+        r = stage_buffer(hd, 1, &dlds);
+    if (r != FMM_OK)
+        return r;
     AdjointArgs a;
     a.dLdT = dL_dT;
-    a.dlds = dL_dslowness;
+    a.dlds = dlds;
     a.mu = hd->adj_mu;
     a.h = hd->params.h;
     a.spd_term = hd->params.spd_term;
@@ -565,6 +658,9 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
     FMM_CUDA(hd, launch_adjoint_persistent(dt, g, s, a, st));
+    if (host_out)
+        FMM_CUDA(hd, cudaMemcpyAsync(dL_dslowness, dlds, natural_cells(hd) * hd->rsize,
+                                     cudaMemcpyDeviceToHost, st));
     FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
     FMM_CUDA(hd, cudaMemsetAsync(hd->adj_count, 0, sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_pending(dt, g, a, hd->adj_count, st));
@@ -584,7 +680,7 @@ fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_
     if (!hd)
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (!T_out || !aligned16(T_out))
-        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned device pointer");
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned pointer");
     if (more_restarts < 0)
         return fail(hd, FMM_ERR_INVALID, "more_restarts must be >= 0");
     if (hd->n_grids)

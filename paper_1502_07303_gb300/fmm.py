@@ -123,9 +123,11 @@ def _stream_handle(stream):
     return ctypes.c_void_p(int(s.cuda_stream))
 
 
-def _dev_ptr(t: torch.Tensor, dtype=None, shape=None, name="array"):
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+def _dev_ptr(t: torch.Tensor, dtype=None, shape=None, name="array", host_ok=False):
+    """Pointer of a contiguous tensor: on the GPU, or also in host memory
+    (pinned or not) for the entry points that copy host arrays themselves."""
+    if not t.is_cuda and not (host_ok and t.device.type == "cpu"):
+        raise ValueError(f"{name} must be a CUDA tensor" + (" or a CPU tensor" if host_ok else ""))
     if dtype is not None and t.dtype != dtype:
         raise ValueError(f"{name} must have dtype {dtype}")
     if shape is not None and tuple(t.shape) != tuple(shape):
@@ -199,7 +201,7 @@ class Solver:
         if isinstance(speed, (int, float)):
             return None, float(speed)
         self._speed_ref = speed
-        return _dev_ptr(speed, self.dtype, self.shape, "speed"), 0.0
+        return _dev_ptr(speed, self.dtype, self.shape, "speed", host_ok=True), 0.0
 
     def _check(self, rc):
         if rc != FMM_OK:
@@ -209,13 +211,14 @@ class Solver:
         p, c = self._speed_args(speed)
         self._check(self.lib.fmm_set_speed(self.handle, p, c))
 
-    def _outputs(self, T_out, tags_out, want_tags):
+    def _outputs(self, T_out, tags_out, want_tags, device="cuda"):
         if T_out is None:
-            T_out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+            T_out = torch.empty(self.shape, dtype=self.dtype, device=device)
         if tags_out is None and want_tags:
-            tags_out = torch.empty(self.shape, dtype=torch.uint8, device="cuda")
-        tp = _dev_ptr(T_out, self.dtype, self.shape, "T_out")
-        gp = None if tags_out is None else _dev_ptr(tags_out, torch.uint8, self.shape, "tags_out")
+            tags_out = torch.empty(self.shape, dtype=torch.uint8, device=T_out.device)
+        tp = _dev_ptr(T_out, self.dtype, self.shape, "T_out", host_ok=True)
+        gp = None if tags_out is None else _dev_ptr(tags_out, torch.uint8, self.shape, "tags_out",
+                                                   host_ok=True)
         return T_out, tags_out, tp, gp
 
     def solve(self, T_out=None, tags_out=None, want_tags=True):
@@ -224,8 +227,8 @@ class Solver:
         return T_out, tags_out
 
     def reinit(self, phi0, T_out=None, tags_out=None, want_tags=True):
-        pp = _dev_ptr(phi0, self.dtype, self.shape, "phi0")
-        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
+        pp = _dev_ptr(phi0, self.dtype, self.shape, "phi0", host_ok=True)
+        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags, phi0.device)
         self._check(self.lib.fmm_reinit_signed_distance(self.handle, pp, tp, gp))
         return T_out, tags_out
 
@@ -251,10 +254,10 @@ class Solver:
         self._check(self.lib.fmm_checkpoint_load(self.handle, buf.ctypes.data, buf.size))
 
     def adjoint(self, dL_dT, out=None):
-        gp = _dev_ptr(dL_dT, self.dtype, self.shape, "dL_dT")
+        gp = _dev_ptr(dL_dT, self.dtype, self.shape, "dL_dT", host_ok=True)
         if out is None:
-            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
-        op = _dev_ptr(out, self.dtype, self.shape, "dL_dslowness")
+            out = torch.empty(self.shape, dtype=self.dtype, device=dL_dT.device)
+        op = _dev_ptr(out, self.dtype, self.shape, "dL_dslowness", host_ok=True)
         self._check(self.lib.fmm_adjoint(self.handle, gp, op))
         return out
 

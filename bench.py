@@ -123,6 +123,75 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """SM clock, its maximum and the clock-event reasons read through NVML
+    (the driver's libnvidia-ml, reads only) every 10 ms from a thread during
+    the timed region; start() returns False when NVML is unavailable."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index, period_s=0.01):
+        self.index, self.period = index, period_s
+        self.rows, self.stop_evt, self.lib, self.dev = [], threading.Event(), None, None
+
+    def start(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(dev)) != 0:
+                return False
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        except Exception:
+            return False
+        self.lib, self.dev, self.ct = lib, dev, ctypes
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return True
+
+    def _sample(self):
+        ct, lib = self.ct, self.lib
+        sm, mx, rs = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        ok = (lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(sm)) == 0 and
+              lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ct.byref(mx)) == 0)   # 1: SM clock
+        if ok:
+            self.reasons_fn(self.dev, ct.byref(rs))
+            self.rows.append((sm.value, mx.value, rs.value))
+
+    def _run(self):
+        while not self.stop_evt.is_set():
+            self._sample()
+            time.sleep(self.period)
+
+    def stop(self):
+        self.stop_evt.set()
+        self.t.join(timeout=2)
+        self._sample()
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+        reasons = sorted({name for _, _, r in self.rows for bit, name in self.REASONS.items() if r & bit})
+        sm = [r[0] for r in self.rows]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[1] for r in self.rows) if self.rows else None,
+                "reasons": reasons, "samples": len(sm), "source": "nvml"}
+
+
+def clock_sampler(index):
+    """NVML sampler, else the nvidia-smi one."""
+    s = NvmlClockSampler(index)
+    if s.start():
+        return s
+    s = ClockSampler(index)
+    s.start()
+    return s
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -385,9 +454,7 @@ def run_gpu(args):
     # fp32: the headline
     barrier(pg)
     torch.cuda.synchronize()
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.start()
+    sampler = clock_sampler(torch.cuda.current_device()) if rank == 0 else None
     t_wall = time.perf_counter()
     if args.part == "f64":
         r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream,

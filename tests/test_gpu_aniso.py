@@ -1,6 +1,5 @@
 """Cells of size dx * dy * dz (Sec. 2.1; the per-axis h_i of Algorithm 11):
 the CUDA path against the oracle on the same seeded inputs."""
-import math
 
 import numpy as np
 import pytest

@@ -218,8 +218,9 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
 // w_i = (h / h_i)^2 (w_x = 1), q = (h/F)^2 and the same shift t = m + u.
 // The per-axis values are sorted together with their weights (and sides);
 // with K = sum w_i, S = sum w_i delta_i and Q = sum w_i delta_i^2 over the
-// set, disc = S^2 - K (Q - q) and u = (S + sqrt(disc)) / K; the largest
-// remaining value is dropped while the set is not causal, as above.
+// set, disc = S^2 - K (Q - q), evaluated as K q - sum_{i<j} w_i w_j
+// (delta_i - delta_j)^2, and u = (S + sqrt(disc)) / K; the largest remaining
+// value is dropped while the set is not causal, as above.
 template <typename real>
 __device__ __forceinline__ void cswap_w(real &a, real &wa, unsigned &ca, real &b, real &wb, unsigned &cb)
 {
@@ -274,8 +275,12 @@ __device__ __forceinline__ real solve_cell_w(const real *kv, int ti, real Tc, re
     for (; nd != 0; --nd) {
         const real K = w0 + w1 + w2;
         const real S = fma(w1, d1, w2 * d2);
-        const real Q = fma(w1 * d1, d1, (w2 * d2) * d2);
-        const real disc = fma(-K, Q - q, S * S);
+        // S^2 - K (Q - q) = K q - sum_{i<j} w_i w_j (delta_i - delta_j)^2
+        // (Lagrange's identity): with unequal weights S^2 and K Q nearly
+        // cancel, the pairwise form does not
+        const real e = d1 - d2;
+        const real P = fma(w0 * w1, d1 * d1, fma(w0 * w2, d2 * d2, (w1 * w2) * (e * e)));
+        const real disc = fma(K, q, -P);
         if (!lt(disc, (real)0)) {
             const real u = vdiv(S + vsqrt(disc), K);
             const real dmax = nd == 3 ? d2 : d1;   // 0 when nd == 1

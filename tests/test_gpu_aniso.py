@@ -130,3 +130,26 @@ def test_spacing_arguments_checked(fmm):
         with pytest.raises(fmm.FmmError) as e:
             s2.restore(image)
         assert e.value.code == fmm.FMM_ERR_INVALID
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_extreme_aspect_ratios(fmm, oracle, dt):
+    """dy = 8 dx and dz = dx / 5 (weights 1/64 and 25 in Algorithm 11)."""
+    h3 = (1.0 / 40, 8.0 / 40, 0.2 / 40)
+    tdt = DT[dt]
+    shape = (30, 12, 33)
+    rng = np.random.default_rng(17)
+    F = wl.fourier_speed(shape, wl.draw_fourier_modes(rng), h=h3)
+    src = wl.random_cells(rng, shape, 2)
+    ref = oracle.solve_sources(shape, src, h3, speed=_q(F, dt))
+    with fmm.Solver(shape, h3, dtype=tdt, speed=torch.as_tensor(F, dtype=tdt, device="cuda"),
+                    sources=src) as s:
+        T, G = s.solve()
+    compare(_host(T), _host(G), ref, dt)
+    x, y, z = wl._axes(shape, h3)
+    c = np.array([0.5 * shape[2] * h3[0], 0.5 * shape[1] * h3[1], 0.5 * shape[0] * h3[2]])
+    phi = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) - 0.35
+    ref = oracle.solve_reinit(_q(phi, dt), h3)
+    with fmm.Solver(shape, h3, dtype=tdt) as s:
+        T, G = s.reinit(torch.as_tensor(phi, dtype=tdt, device="cuda"))
+    compare(_host(T), _host(G), ref, dt)

@@ -4,7 +4,8 @@
  *
  * The library solves the Eikonal equation |grad psi| F = 1 (Eq. (1) of Yang &
  * Stern, "A highly scalable massively parallel fast marching method for the
- * Eikonal equation") on a uniform cell-centred 3-D grid with the first-order
+ * Eikonal equation") on a cell-centred 3-D grid of cells dx * dy * dz (uniform
+ * in each direction, Sec. 2.1) with the first-order
  * Godunov upwind scheme of Eq. (2)-(3), by the restarted narrow band method
  * of Algorithm 16: subdomains (here 8x8x8 bricks of the grid) march locally up
  * to a global bound that rises by a stride at every restart, exchange changed
@@ -187,11 +188,13 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
 /*
  * fmm_adjoint -- reverse-mode derivative of a scalar loss L(psi) with respect
  * to the slowness 1/F of every cell, about the last solve on this handle
- * (which must have been run with record_tape = 1; otherwise FMM_ERR_STATE).
- * The discrete Eq. (2) at an accepted non-FIX cell p with final upwind set
- * U(p) reads sum_{i in U(p)} ((psi_p - psi_i)/h)^2 = s_p^2, which gives
- * dpsi_p/ds_p = s_p/D_p and dpsi_p/dpsi_i = (psi_p - psi_i)/(h^2 D_p) with
- * D_p = sum_i (psi_p - psi_i)/h^2; these are applied in decreasing psi.
+ * (which must have been run with record_tape = 1 and have finished;
+ * otherwise FMM_ERR_STATE).  The discrete Eq. (2) at an accepted non-FIX
+ * cell p with final upwind set U(p) reads sum_{i in U(p)} ((psi_p -
+ * psi_i)/h_i)^2 = s_p^2 (h_i the cell size along the axis of neighbour i),
+ * which gives dpsi_p/ds_p = s_p/D_p and dpsi_p/dpsi_i = (psi_p - psi_i) /
+ * (h_i^2 D_p) with D_p = sum_i (psi_p - psi_i)/h_i^2; these are applied in
+ * decreasing psi.
  * FIX cells get zero.  dL_dT: device (dtype), dL/dpsi; dL_dslowness: device
  * (dtype), written.  (This derivative is not part of the paper.)
  */

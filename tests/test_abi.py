@@ -83,3 +83,50 @@ def test_binding_structs_match_header():
     for cname, pyst in (("fmm_config", fmm.FmmConfig), ("fmm_stats", fmm.FmmStats),
                         ("fmm_trace_entry", fmm.FmmTraceEntry)):
         assert [f[0] for f in pyst._fields_] == _struct_fields(cname), cname
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "fmm.h"
+
+int main(void)
+{
+    fmm_config cfg;
+    fmm_handle *h = NULL;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.nx = cfg.ny = cfg.nz = 8;
+    cfg.h = 0.125;
+    cfg.hy = -1.0;                   /* negative cell size: rejected */
+    cfg.dtype = FMM_F32;
+    if (fmm_create(&cfg, NULL, 1.0, NULL, 0, &h) != FMM_ERR_INVALID || h != NULL)
+        return 1;
+    if (strlen(fmm_last_error(NULL)) == 0)
+        return 2;
+    int64_t bytes = 0;
+    if (fmm_checkpoint_size(NULL, &bytes) != FMM_ERR_INVALID)
+        return 3;
+    printf("%zu %zu\n", sizeof(fmm_config), sizeof(fmm_stats));
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(tmp_path):
+    """include/fmm.h is plain C11 (warnings are errors): a C caller compiles
+    against it, links the library, gets argument errors without a GPU, and
+    sees the struct sizes the binding uses."""
+    import subprocess
+    from paper_1502_07303_gb300 import build, fmm
+    lib = build.build()
+    src = tmp_path / "caller.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe), lib,
+                    f"-Wl,-rpath,{os.path.dirname(lib)}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    cfg_size, stats_size = (int(v) for v in r.stdout.split())
+    assert cfg_size == ctypes.sizeof(fmm.FmmConfig)
+    assert stats_size == ctypes.sizeof(fmm.FmmStats)

@@ -343,13 +343,15 @@ def _events(torch, stream):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1):
+def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1, dtypes=("f32", "f64")):
     """Heterogeneous speed F = exp(g/2) (16 random Fourier modes), 8 point
     sources, L = sum of psi at 64 receiver cells: forward solve with the tape
     and fmm_adjoint (dL/d slowness), each timed with CUDA events."""
     p = wl.fourier_sources(n=n, n_sources=8, n_receivers=64, seed=3, device="cuda")
     out = {"workload": f"fourier speed {n}^3, 8 sources, 64 receivers", "points": p.n_points}
     for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        if name not in dtypes:
+            continue
         F = p.speed.to(dt).contiguous()
         g = torch.zeros(p.shape, dtype=dt, device="cuda")
         for i, j, k in p.receivers:
@@ -430,6 +432,14 @@ def run_gpu(args):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
+    if args.part.startswith("adjoint"):
+        # only the forward + adjoint pair of one dtype (for profiling)
+        dt = args.part.split("-")[1]
+        r = measure_adjoint(fmm, torch, wl, stream, n=args.adjoint_n, steps=args.steps,
+                            warmup=args.warmup, dtypes=(dt,))
+        if rank == 0:
+            print(json.dumps({"part": args.part, **r}), flush=True)
+        return 0
     n = args.n
     p = wl.random_spheres(n=n, count=N_SPHERES, seed=SEED, device="cuda")
     phi64 = p.phi0.contiguous()
@@ -565,8 +575,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID, help=argparse.SUPPRESS)
-    ap.add_argument("--part", default="all", choices=["all", "f32", "f64"],
-                    help="f32 / f64: only the timed solves of one dtype (for profiling)")
+    ap.add_argument("--part", default="all", choices=["all", "f32", "f64", "adjoint-f32", "adjoint-f64"],
+                    help="f32 / f64: only the timed solves of one dtype; adjoint-f32 / "
+                         "adjoint-f64: only the forward + adjoint pair (for profiling)")
+    ap.add_argument("--adjoint-n", type=int, default=512,
+                    help="grid size of the adjoint workload of --part adjoint-*")
     ap.add_argument("--params", type=_params, default=None,
                     help="restart parameters as JSON (skips the autotuner), e.g. "
                          "'{\"schedule\": 2, \"stride\": \"inf\"}'")

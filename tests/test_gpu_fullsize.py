@@ -90,10 +90,11 @@ def sampled_local_solves(oracle, T, G, h, F, n=3000, seed=0):
 
 
 # the library defaults, and the configurations the bench's autotuner picks
-# for this workload (persistent without restarts; continuous at 2 h without a
-# lead limit)
+# for this workload (persistent without restarts; continuous at 2 h or 4 h
+# without a lead limit)
 BENCH_PARAMS = [{}, {"schedule": 2, "stride": math.inf},
-                {"schedule": 3, "stride": 2.0, "max_lead": 1 << 20}]
+                {"schedule": 3, "stride": 2.0, "max_lead": 1 << 20},
+                {"schedule": 3, "stride": 4.0, "max_lead": 1 << 20}]
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +103,8 @@ def c2():
     return p, {}
 
 
-@pytest.mark.parametrize("params", BENCH_PARAMS, ids=["defaults", "persistent-inf", "continuous-2h"])
+@pytest.mark.parametrize("params", BENCH_PARAMS,
+                         ids=["defaults", "persistent-inf", "continuous-2h", "continuous-4h"])
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_bench_workload_256_full_compare(fmm, oracle, c2, dt, params):
     p, refs = c2

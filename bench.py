@@ -1,11 +1,13 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 restarted narrow band fast marching library.
 
-Workload (one "step" = one complete solve through the C ABI): two-sided
-signed-distance reinitialisation of 32 seeded random spheres with the
-sin-modulated level set on a 256^3 unit cube (16.8 M points), fp32, full
-march, the library's default restart parameters.  The metric is grid points finalised per second (Gpoints/s).
-fp64 is measured on the same workload and reported beside it.
+Headline workload (one "step" = one complete solve through the C ABI):
+signed-distance reinitialisation of one sphere of radius 0.3 centred in a
+1024^3 unit cube (1.07 G points), full march, fp64 (the paper's precision),
+with the restart parameters the library's autotuner picks for it.  The metric
+is grid points finalised per second (Gpoints/s).  Beside it: the same solve in
+fp32, the 256^3 32-sphere reinitialisation, the 64^3 point source, the 512^3
+heterogeneous-speed forward solve and its adjoint, and the 256-grid batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -33,14 +35,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpoints/s finalised (fp32/fp64) and % HBM roofline; adjoint and batched vs plain"
 UNIT = "Gpoints/s"
-N_GRID = 256
-N_SPHERES = 32
-SEED = 2
-# algorithmic bytes per finalised point of a reinitialisation: read phi0,
-# write psi and the tag once (fp32: 4 + 4 + 1, fp64: 8 + 8 + 1)
-ALG_BYTES = {"f32": 9, "f64": 17}
-REF_SAMPLE_N = 128          # oracle sample grid for the reference arm
-CPU_BASELINE_N = 192        # oracle sample grid for the cpu_baseline entry
+N_GRID = 1024               # headline: single sphere, 1024^3
+RADIUS = 0.3
+N_C2, N_SPHERES, SEED = 256, 32, 2
+# algorithmic bytes per finalised point: a reinitialisation reads phi0 and
+# writes psi and the tag once (fp32: 4 + 4 + 1, fp64: 8 + 8 + 1); a point-
+# source solve with constant speed writes psi and the tag; a heterogeneous
+# solve also reads F
+ALG_BYTES = {"reinit": {"f32": 9, "f64": 17}, "sources": {"f32": 5, "f64": 9},
+             "sources_speed": {"f32": 9, "f64": 17}}
+REF_SAMPLE_N = 192          # oracle sample grid of the reference arm
+CPU_BASELINE_N = 256        # oracle sample grid of the cpu_baseline entry
 
 
 def peaks():
@@ -52,22 +57,33 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel, dtype):
-    """DRAM bytes per finalised point of a march kernel and dtype from the
-    committed ncu summary (lines "kernel dtype source_sha256_16 bytes"), valid
-    only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "k_march_traffic.txt")
+def _profile_record(fname, kernel, dtype, workload):
+    """A per-point figure of a march kernel from a committed ncu summary
+    (lines "kernel dtype workload source_sha256_16 value"), valid only while
+    the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", fname)
     src = os.path.join(ROOT, "paper_1502_07303_gb300", "csrc", "fmm_march.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(path):
             f = line.split()
-            if len(f) == 4 and not line.startswith("#") and f[0] == kernel and f[1] == dtype \
-                    and f[2] == sha:
-                return float(f[3])
+            if len(f) == 5 and not line.startswith("#") and f[0] == kernel and f[1] == dtype \
+                    and f[2] == workload and f[3] == sha:
+                return float(f[4])
         return None
     except Exception:
         return None
+
+
+def traffic_record(kernel, dtype, workload):
+    """DRAM bytes (read + write) per finalised point."""
+    return _profile_record("k_march_traffic.txt", kernel, dtype, workload)
+
+
+def ops_record(kernel, dtype, workload):
+    """fp64 flops (fp64 kernels) or issued warp instructions (fp32 kernels)
+    per finalised point."""
+    return _profile_record("k_march_ops.txt", kernel, dtype, workload)
 
 
 class ClockSampler:
@@ -237,11 +253,12 @@ def sum_over_ranks(pg, v):
 # ---------------------------------------------------------------------------
 
 def oracle_rate(n):
-    """One oracle solve of the workload recipe at n^3; returns (Gpoints/s, s)."""
+    """One oracle solve of the headline recipe (single sphere) at n^3;
+    returns (Gpoints/s, s)."""
     import oracle
     from paper_1502_07303_gb300 import workloads as wl
     oracle.build()
-    p = wl.random_spheres(n=n, count=N_SPHERES, seed=SEED)
+    p = wl.single_sphere(n=n, radius=RADIUS)
     t0 = time.perf_counter()
     oracle.solve_reinit(p.phi0, p.h)
     dt = time.perf_counter() - t0
@@ -255,7 +272,7 @@ def run_reference(args):
     import oracle
     from paper_1502_07303_gb300 import workloads as wl
     oracle.build()
-    p = wl.random_spheres(n=REF_SAMPLE_N, count=N_SPHERES, seed=SEED)
+    p = wl.single_sphere(n=REF_SAMPLE_N, radius=RADIUS)
     for _ in range(args.warmup):
         oracle.solve_reinit(p.phi0, p.h)
     times = []
@@ -265,14 +282,14 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = p.n_points / (ms / 1e3) / 1e9
-    sample = (f"{N_SPHERES}-sphere reinitialisation recipe at {REF_SAMPLE_N}^3 "
+    sample = (f"single-sphere reinitialisation recipe (r = {RADIUS}) at {REF_SAMPLE_N}^3 "
               f"({p.n_points} points) per step, oracle fp64, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"reinit random_spheres{N_SPHERES} {N_GRID}^3 (sampled at "
-                                   f"{REF_SAMPLE_N}^3)", "seed": SEED},
+            "config": {"workload": f"reinit single sphere r={RADIUS} {N_GRID}^3 (sampled at "
+                                   f"{REF_SAMPLE_N}^3)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -285,25 +302,35 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream, params):
-    """Device-timed solves: CUDA events around each solve on the solve's
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure(fmm, torch, p, dtype, steps, warmup, flush, stream, params, phi=None, speed=None):
+    """Device-timed solves of problem p (reinitialisation of phi, or a
+    point-source solve): CUDA events around each solve on the solve's
     stream, L2 flushed (256 MiB write) before every step, outside the events."""
-    shape = p.shape
-    s = fmm.Solver(shape, p.h, dtype=dtype, time_kernels=True, stream=stream, **params)
-    T_out = torch.empty(shape, dtype=dtype, device="cuda")
-    G_out = torch.empty(shape, dtype=torch.uint8, device="cuda")
+    s = fmm.Solver(p.shape, p.h, dtype=dtype, time_kernels=True, stream=stream, speed=speed,
+                   sources=None if phi is not None else p.sources, tuned=False, **params)
+    T_out = torch.empty(p.shape, dtype=dtype, device="cuda")
+    G_out = torch.empty(p.shape, dtype=torch.uint8, device="cuda")
+
+    def solve():
+        if phi is not None:
+            s.reinit(phi, T_out, G_out)
+        else:
+            s.solve(T_out, G_out)
     for _ in range(warmup):
         flush.fill_(1)
-        s.reinit(phi_dev, T_out, G_out)
+        solve()
     torch.cuda.synchronize()
     step_ms, march_ms, march_l, launches = [], 0.0, 0, 0
     stats = None
     for _ in range(steps):
         flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record(stream)
-        s.reinit(phi_dev, T_out, G_out)
+        solve()
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -312,22 +339,20 @@ def measure(fmm, torch, phi_dev, p, dtype, steps, warmup, flush, stream, params)
         march_l += stats["march_launches"]
         launches += stats["kernel_launches"]
     s.close()
+    del T_out, G_out
     return {"ms": statistics.mean(step_ms), "ms_min": min(step_ms), "march_ms": march_ms / steps,
-            "march_launches": march_l / steps, "launches": launches, "stats": stats,
-            "T": T_out}
+            "march_launches": march_l / steps, "launches": launches, "stats": stats}
 
 
 def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream, params):
     """The user's call with host buffers: fmm_reinit_signed_distance takes
     pinned host phi0 and psi, copies phi0 to the device, solves and copies
     psi back before it returns, all inside the timed region of every step."""
-    shape = p.shape
-    s = fmm.Solver(shape, p.h, dtype=dtype, stream=stream, **params)
-    T_host = torch.empty(shape, dtype=dtype, pin_memory=True)
+    s = fmm.Solver(p.shape, p.h, dtype=dtype, stream=stream, tuned=False, **params)
+    T_host = torch.empty(p.shape, dtype=dtype, pin_memory=True)
     times = []
     for k in range(warmup + steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record(stream)
         s.reinit(phi_host, T_host, None, want_tags=False)
         e1.record(stream)
@@ -339,63 +364,77 @@ def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream, params):
     return statistics.mean(times), nbytes, T_host.numel() * T_host.element_size()
 
 
-def _events(torch, stream):
-    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
-def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1, dtypes=("f32", "f64")):
+def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1, dtypes=("f32", "f64"),
+                    params=None):
     """Heterogeneous speed F = exp(g/2) (16 random Fourier modes), 8 point
     sources, L = sum of psi at 64 receiver cells: forward solve with the tape
-    and fmm_adjoint (dL/d slowness), each timed with CUDA events."""
+    and fmm_adjoint (dL/d slowness), each timed with CUDA events; the plain
+    forward solve without a tape beside them."""
     p = wl.fourier_sources(n=n, n_sources=8, n_receivers=64, seed=3, device="cuda")
     out = {"workload": f"fourier speed {n}^3, 8 sources, 64 receivers", "points": p.n_points}
     for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
         if name not in dtypes:
             continue
+        prm = (params or {}).get(name, {})
         F = p.speed.to(dt).contiguous()
         g = torch.zeros(p.shape, dtype=dt, device="cuda")
         for i, j, k in p.receivers:
             g[k, j, i] += 1.0
         s = fmm.Solver(p.shape, p.h, dtype=dt, speed=F, sources=p.sources, record_tape=True,
-                       stream=stream)
+                       stream=stream, tuned=False, **prm)
+        plain = fmm.Solver(p.shape, p.h, dtype=dt, speed=F, sources=p.sources, stream=stream,
+                           tuned=False, **prm)
         T = torch.empty(p.shape, dtype=dt, device="cuda")
         d = torch.empty(p.shape, dtype=dt, device="cuda")
-        fw, bw = [], []
+        fw, bw, pl = [], [], []
         for k in range(warmup + steps):
-            e0, e1 = _events(torch, stream)
-            e2, e3 = _events(torch, stream)
+            e0, e1 = _events(torch)
             e0.record(stream)
-            s.solve(T, None, want_tags=False)
+            plain.solve(T, None, want_tags=False)
             e1.record(stream)
+            e2, e3 = _events(torch)
+            e4, e5 = _events(torch)
             e2.record(stream)
-            s.adjoint(g, d)
+            s.solve(T, None, want_tags=False)
             e3.record(stream)
-            e3.synchronize()
+            e4.record(stream)
+            s.adjoint(g, d)
+            e5.record(stream)
+            e5.synchronize()
             if k >= warmup:
-                fw.append(e0.elapsed_time(e1))
-                bw.append(e2.elapsed_time(e3))
+                pl.append(e0.elapsed_time(e1))
+                fw.append(e2.elapsed_time(e3))
+                bw.append(e4.elapsed_time(e5))
         st = s.stats()
         s.close()
-        fms, bms = statistics.mean(fw), statistics.mean(bw)
-        out[name] = {"forward_gpts": p.n_points / fms / 1e6, "adjoint_gpts": p.n_points / bms / 1e6,
-                     "forward_ms": fms, "adjoint_ms": bms, "adjoint_vs_forward": fms / bms,
-                     "adjoint_iterations": st["adjoint_iterations"]}
+        plain.close()
+        pms, fms, bms = statistics.mean(pl), statistics.mean(fw), statistics.mean(bw)
+        out[name] = {"forward_gpts": p.n_points / pms / 1e6, "forward_ms": pms,
+                     "forward_tape_ms": fms, "adjoint_gpts": p.n_points / bms / 1e6,
+                     "adjoint_ms": bms, "adjoint_vs_forward": pms / bms,
+                     "adjoint_iterations": st["adjoint_iterations"], "params": prm}
     return out
 
 
-def measure_batch(fmm, torch, wl, stream, steps=2, warmup=1):
+def measure_batch(fmm, torch, wl, autotune, stream, steps=2, warmup=1, tune=True):
     """256 independent grids (each axis uniform in [32, 192]), 1-8 random
-    spheres each, fp32: one batched solve against the same grids solved one
-    after another with single-grid handles."""
+    spheres each, fp32: one batched solve (restart parameters from the batch
+    autotuner) against the same grids solved one after another with
+    single-grid handles."""
     probs = wl.batch(n_grids=256, lo=32, hi=192, seed=4, device="cuda")
     phis = [p.phi0.to(torch.float32).contiguous() for p in probs]
     pts = sum(p.n_points for p in probs)
+    best, table = {}, []
+    if tune:
+        best, _, table = autotune.tune_batch(probs, torch.float32, search=autotune.QUICK, reps=2,
+                                             save=False, stream=stream)
+        best = best or {}
     b = fmm.Batch([p.shape for p in probs], [p.h for p in probs], dtype=torch.float32,
-                  stream=stream)
+                  stream=stream, tuned=False, **best)
     Ts = [torch.empty(p.shape, dtype=torch.float32, device="cuda") for p in probs]
     tb = []
     for k in range(warmup + steps):
-        e0, e1 = _events(torch, stream)
+        e0, e1 = _events(torch)
         e0.record(stream)
         b.reinit(phis, Ts, None, want_tags=False)
         e1.record(stream)
@@ -404,10 +443,11 @@ def measure_batch(fmm, torch, wl, stream, steps=2, warmup=1):
             tb.append(e0.elapsed_time(e1))
     st = b.stats()
     b.close()
-    solvers = [fmm.Solver(p.shape, p.h, dtype=torch.float32, stream=stream) for p in probs]
+    solvers = [fmm.Solver(p.shape, p.h, dtype=torch.float32, stream=stream, tuned=False, **best)
+               for p in probs]
     tp = []
     for k in range(warmup + steps):
-        e0, e1 = _events(torch, stream)
+        e0, e1 = _events(torch)
         e0.record(stream)
         for s, ph, T in zip(solvers, phis, Ts):
             s.reinit(ph, T, None, want_tags=False)
@@ -421,13 +461,63 @@ def measure_batch(fmm, torch, wl, stream, steps=2, warmup=1):
     return {"workload": "256 grids, axes uniform in [32, 192], 1-8 spheres each, fp32",
             "points": pts, "batched_gpts": pts / bms / 1e6, "batched_ms": bms,
             "plain_gpts": pts / pms / 1e6, "plain_ms": pms, "batched_vs_plain": pms / bms,
-            "restarts": st["restarts"], "bricks": st["n_bricks"]}
+            "restarts": st["restarts"], "bricks": st["n_bricks"],
+            "params": dict(best, brick=8, chosen_by="autotune.tune_batch(QUICK) before timing"),
+            "tune_ms": [[c, None if ms is None else round(ms, 3)] for c, ms in table]}
+
+
+def tune_params(autotune, torch, p, dt, stream, kind, search=None):
+    best, _, table = autotune.tune(p, dt, kind=kind, search=search or autotune.QUICK, reps=2,
+                                   save=False, stream=stream)
+    return best or {}, [[c, None if ms is None else round(ms, 3)] for c, ms in table]
+
+
+def roofline_hbm(r, pts, alg, kernel, dt, workload, peak, peak_kind):
+    """HBM roofline of the dominant kernel: algorithmic bytes of one launch
+    over its average CUDA-event duration, against the measured copy peak."""
+    launches = max(r["march_launches"], 1.0)
+    avg_s = r["march_ms"] / launches / 1e3
+    achieved = alg * pts / launches / avg_s / 1e9 if avg_s > 0 else 0.0
+    bpp = traffic_record(kernel, dt, workload)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": (bpp * pts / launches) if bpp else None,
+            "kernel": kernel, "peak_kind": peak_kind, "alg_bytes_per_point": alg,
+            "avg_launch_us": 1e3 * r["march_ms"] / launches,
+            "launches_per_step": r["march_launches"], "share_of_step": r["march_ms"] / r["ms"]}
+
+
+def roofline_alu(r, pts, kernel, dt, workload, fp64_peak, sms, sm_mhz):
+    """Arithmetic roofline of the dominant kernel.  fp64: double flops per
+    launch (ncu counts per point x points) over the launch time, against the
+    measured double FMA rate (fmm_probe_fma_rate).  fp32: issued warp
+    instructions per launch over the launch time, against the issue rate of
+    the SMs (4 schedulers x 1 warp instruction per clock x SMs x max clock)."""
+    launches = max(r["march_launches"], 1.0)
+    avg_s = r["march_ms"] / launches / 1e3
+    per_pt = ops_record(kernel, dt, workload)
+    if dt == "f64":
+        peak = fp64_peak / 1e12 if fp64_peak else None
+        ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None
+        return {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": (ach / peak) if (ach and peak) else None, "kernel": kernel,
+                "peak_kind": "measured (fmm_probe_fma_rate, double FMA chains)",
+                "ops_per_point": per_pt}
+    peak = 4 * sms * sm_mhz * 1e6 / 1e12
+    ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None
+    return {"bound": "alu", "pipe": "issue", "achieved": ach, "peak": peak, "unit": "Tinst/s",
+            "frac": (ach / peak) if ach else None, "kernel": kernel,
+            "peak_kind": f"derived: 4 warp instructions per clock per SM x {sms} SMs x {sm_mhz:.0f} MHz",
+            "ops_per_point": per_pt}
+
+
+def kernel_name(params):
+    return {1: "k_march", 2: "k_march_persistent"}.get(params.get("schedule", 0), "k_march_continuous")
 
 
 def run_gpu(args):
     ws, rank, local, pg = dist_setup()
     import torch
-    from paper_1502_07303_gb300 import fmm
+    from paper_1502_07303_gb300 import autotune, fmm
     from paper_1502_07303_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
@@ -435,129 +525,161 @@ def run_gpu(args):
     if args.part.startswith("adjoint"):
         # only the forward + adjoint pair of one dtype (for profiling)
         dt = args.part.split("-")[1]
+        prm = {dt: dict(args.params)} if args.params is not None else None
         r = measure_adjoint(fmm, torch, wl, stream, n=args.adjoint_n, steps=args.steps,
-                            warmup=args.warmup, dtypes=(dt,))
+                            warmup=args.warmup, dtypes=(dt,), params=prm)
         if rank == 0:
             print(json.dumps({"part": args.part, **r}), flush=True)
         return 0
-    n = args.n
-    p = wl.random_spheres(n=n, count=N_SPHERES, seed=SEED, device="cuda")
-    phi64 = p.phi0.contiguous()
-    phi32 = phi64.to(torch.float32).contiguous()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    pts = p.n_points
+    DTS = {"f32": torch.float32, "f64": torch.float64}
 
-    # restart parameters: the library's autotuner on this workload, before
-    # any timed region (persistent schedule over strides, phased at default)
-    from paper_1502_07303_gb300 import autotune
+    if args.part in ("c2-f32", "c2-f64", "c5-f32", "c5-f64"):
+        # one timed solve series of one workload and dtype (for profiling)
+        w, name = args.part.split("-")
+        n = args.n or (N_C2 if w == "c2" else N_GRID)
+        p = (wl.random_spheres(n=n, count=N_SPHERES, seed=SEED, device="cuda") if w == "c2"
+             else wl.single_sphere(n=n, radius=RADIUS, device="cuda"))
+        phi = p.phi0.to(DTS[name]).contiguous()
+        prm = dict(args.params) if args.params is not None else {}
+        r = measure(fmm, torch, p, DTS[name], args.steps, args.warmup, flush, stream, prm, phi=phi)
+        if rank == 0:
+            print(json.dumps({"part": args.part, "n": n, "ms_per_step": r["ms"], "params": prm,
+                              "march_ms": r["march_ms"], "march_launches": r["march_launches"],
+                              "stats": r["stats"]}), flush=True)
+        return 0
+
+    n = args.n or N_GRID
+    p = wl.single_sphere(n=n, radius=RADIUS, device="cuda")
+    pts = p.n_points
     tuned, tune_tables = {}, {}
-    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+    phis = {"f64": p.phi0.contiguous(), "f32": p.phi0.to(torch.float32).contiguous()}
+    for name in ("f64", "f32"):
         if args.params is not None:
             tuned[name] = dict(args.params)
             continue
-        best, best_ms, table = autotune.tune(p, dt, kind="reinit", search=autotune.QUICK, reps=2,
-                                             save=False, stream=stream)
-        tuned[name] = best or {}
-        tune_tables[name] = [[c, None if ms is None else round(ms, 3)] for c, ms in table]
+        tuned[name], tune_tables[name] = tune_params(autotune, torch, p, DTS[name], stream, "reinit")
 
-    # fp32: the headline
+    # the headline: fp64, then fp32 on the same workload
     barrier(pg)
     torch.cuda.synchronize()
     sampler = clock_sampler(torch.cuda.current_device()) if rank == 0 else None
     t_wall = time.perf_counter()
-    if args.part == "f64":
-        r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream,
-                      tuned["f64"])
-        if sampler:
-            sampler.stop()
-        if rank == 0:
-            print(json.dumps({"part": "f64", "ms_per_step": r64["ms"], "params": tuned["f64"],
-                              "march_ms": r64["march_ms"], "march_launches": r64["march_launches"],
-                              "stats": r64["stats"]}), flush=True)
-        return 0
-    r32 = measure(fmm, torch, phi32, p, torch.float32, args.steps, args.warmup, flush, stream,
-                  tuned["f32"])
+    r64 = measure(fmm, torch, p, torch.float64, args.steps, args.warmup, flush, stream,
+                  tuned["f64"], phi=phis["f64"])
     torch.cuda.synchronize()
     barrier(pg)
     wall_ms = 1e3 * (time.perf_counter() - t_wall)
     clocks = sampler.stop() if sampler else None
-    ms32 = max_over_ranks(pg, r32["ms"])
-    total_pts = sum_over_ranks(pg, float(pts))
-    value = total_pts / (ms32 / 1e3) / 1e9
-    if args.part == "f32":
-        if rank == 0:
-            print(json.dumps({"part": "f32", "value": value, "unit": UNIT, "ms_per_step": ms32,
-                              "params": tuned["f32"], "march_ms": r32["march_ms"],
-                              "march_launches": r32["march_launches"],
-                              "stats": r32["stats"]}), flush=True)
-        return 0
-
-    # fp64 on the same workload
-    r64 = measure(fmm, torch, phi64, p, torch.float64, args.steps, args.warmup, flush, stream,
-                  tuned["f64"])
     ms64 = max_over_ranks(pg, r64["ms"])
+    total_pts = sum_over_ranks(pg, float(pts))
+    value = total_pts / (ms64 / 1e3) / 1e9
+    r32 = measure(fmm, torch, p, torch.float32, args.steps, args.warmup, flush, stream,
+                  tuned["f32"], phi=phis["f32"])
+    ms32 = max_over_ranks(pg, r32["ms"])
 
-    # end to end through the public API with host buffers (fp32)
-    phi_host = phi32.cpu().pin_memory()
-    e2e_ms, h2d, d2h = measure_e2e(fmm, torch, phi_host, p, torch.float32, args.steps,
-                                   args.warmup, stream, tuned["f32"])
+    # end to end through the public API with host buffers (fp64)
+    phi_host = phis["f64"].cpu().pin_memory()
+    del phis
+    e2e_ms, h2d, d2h = measure_e2e(fmm, torch, phi_host, p, torch.float64, args.steps,
+                                   args.warmup, stream, tuned["f64"])
+    del phi_host
     e2e_ms = max_over_ranks(pg, e2e_ms)
     e2e_value = total_pts / (e2e_ms / 1e3) / 1e9
+    del p
+    torch.cuda.empty_cache()
 
-    adjoint = measure_adjoint(fmm, torch, wl, stream)
-    batched = measure_batch(fmm, torch, wl, stream)
+    others = {}
+    if not args.quick:
+        # the 256^3 32-sphere reinitialisation and the 64^3 point source
+        c2 = wl.random_spheres(n=N_C2, count=N_SPHERES, seed=SEED, device="cuda")
+        others["c2"] = {"workload": f"reinit random_spheres{N_SPHERES} {N_C2}^3",
+                        "points": c2.n_points}
+        for name in ("f32", "f64"):
+            phi = c2.phi0.to(DTS[name]).contiguous()
+            prm, tab = tune_params(autotune, torch, c2, DTS[name], stream, "reinit")
+            r = measure(fmm, torch, c2, DTS[name], args.steps, args.warmup, flush, stream, prm,
+                        phi=phi)
+            others["c2"][name] = {"gpts": c2.n_points / r["ms"] / 1e6, "ms": r["ms"], "params": prm,
+                                  "accepted_per_point": r["stats"]["accepted"] / c2.n_points,
+                                  "solves_per_point": r["stats"]["cell_solves"] / c2.n_points,
+                                  "marches_per_brick": r["stats"]["brick_marches"] / r["stats"]["n_bricks"]}
+        del c2, phi
+        c1 = wl.point_source(64)
+        prm, _ = tune_params(autotune, torch, c1, torch.float64, stream, "sources")
+        r = measure(fmm, torch, c1, torch.float64, args.steps, args.warmup, flush, stream, prm)
+        others["c1"] = {"workload": "point source at cell (32, 32, 32) of 64^3, F = 1, fp64",
+                        "points": c1.n_points, "gpts": c1.n_points / r["ms"] / 1e6, "ms": r["ms"],
+                        "params": prm}
+        adj_params = {}
+        c3 = wl.fourier_sources(n=512, n_sources=8, n_receivers=64, seed=3, device="cuda")
+        for name in ("f32", "f64"):
+            c3t = wl.Problem(c3.name, c3.shape, c3.h, sources=c3.sources,
+                             speed=c3.speed.to(DTS[name]).contiguous())
+            adj_params[name], _ = tune_params(autotune, torch, c3t, DTS[name], stream, "sources_speed")
+            del c3t
+        del c3
+        torch.cuda.empty_cache()
+        others["adjoint"] = measure_adjoint(fmm, torch, wl, stream, params=adj_params)
+        others["batched"] = measure_batch(fmm, torch, wl, autotune, stream)
 
     if rank != 0:
         return 0
-
     peak, peak_kind = peaks()
-
-    def roofline(r, dt):
-        kernel = {1: "k_march", 2: "k_march_persistent"}.get(tuned[dt].get("schedule", 0),
-                                                              "k_march_continuous")
-        launches = max(r["march_launches"], 1.0)
-        avg_launch_s = r["march_ms"] / launches / 1e3
-        alg_per_launch = ALG_BYTES[dt] * pts / launches
-        achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-        bpp = traffic_record(kernel, dt)
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": (bpp * pts / launches) if bpp else None,
-                "kernel": kernel, "peak_kind": peak_kind,
-                "avg_launch_us": 1e3 * r["march_ms"] / launches,
-                "launches_per_step": r["march_launches"],
-                "share_of_step": r["march_ms"] / r["ms"]}
-
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    try:
+        sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        sm_mhz = 2070.0
+    fp64_peak = fmm.probe_fma_rate(torch.float64, iters=1 << 15)
+    fp32_fma_peak = fmm.probe_fma_rate(torch.float32, iters=1 << 20)
+    wname = f"sphere{n}"
+    k64, k32 = kernel_name(tuned["f64"]), kernel_name(tuned["f32"])
     cpu_rate, cpu_s = oracle_rate(CPU_BASELINE_N) if ws == 1 else (None, None)
-    st = r32["stats"]
+    st = r64["stats"]
+    st32 = r32["stats"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"reinit random_spheres{N_SPHERES} {n}^3", "grid": [n, n, n],
-                   "points_per_gpu": pts, "seed": SEED,
-                   "restart_params": {"f32": tuned["f32"], "f64": tuned["f64"],
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"reinit single sphere r={RADIUS} centred, {n}^3 unit cube, full march",
+                   "grid": [n, n, n], "points_per_gpu": pts,
+                   "restart_params": {"f64": tuned["f64"], "f32": tuned["f32"],
                                       "chosen_by": ("given with --params" if args.params is not None
                                                     else "autotune.QUICK on this workload before "
                                                          "timing (ms per candidate in tune_ms)"),
                                       "tune_ms": tune_tables},
-                   "brick": 8, "l2": "flushed before every step (256 MiB write)",
+                   "brick": 8, "l2": "inputs (phi0 8.6 GB fp64) larger than L2; also flushed "
+                                     "before every step (256 MiB write)",
                    "replicas": ws, "parallelism": "independent replicas, no collective"},
-        "roofline": roofline(r32, "f32"),
+        "roofline": roofline_hbm(r64, pts, ALG_BYTES["reinit"]["f64"], k64, "f64", wname, peak,
+                                 peak_kind),
+        "roofline_alu": roofline_alu(r64, pts, k64, "f64", wname, fp64_peak, sms, sm_mhz),
         "cpu_baseline": ({"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                          "sample": f"{N_SPHERES}-sphere reinitialisation recipe at "
-                                    f"{CPU_BASELINE_N}^3, oracle fp64, 1 thread, {cpu_s:.1f} s"}
+                          "sample": f"single-sphere reinitialisation recipe at {CPU_BASELINE_N}^3 "
+                                    f"({CPU_BASELINE_N ** 3} points), oracle fp64, 1 thread, "
+                                    f"{cpu_s:.1f} s"}
                          if cpu_rate is not None else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": r32["launches"],
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "call": "fmm_reinit_signed_distance with pinned host phi0 and psi (fp64)"},
+        "gpu_launches": r64["launches"],
         "clocks": clocks,
-        "fp64": {"value": total_pts / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
-                 "roofline": roofline(r64, "f64")},
-        "adjoint": adjoint,
-        "batched": batched,
+        "fp32": {"value": total_pts / (ms32 / 1e3) / 1e9, "ms_per_step": ms32,
+                 "roofline": roofline_hbm(r32, pts, ALG_BYTES["reinit"]["f32"], k32, "f32", wname,
+                                          peak, peak_kind),
+                 "roofline_alu": roofline_alu(r32, pts, k32, "f32", wname, fp64_peak, sms, sm_mhz),
+                 "solve_stats": {k: st32[k] for k in ("restarts", "brick_marches", "march_rounds",
+                                                      "accepted", "cell_solves", "n_bricks")}},
+        "peaks_measured_here": {"fp64_fma_tflops": fp64_peak / 1e12,
+                                "fp32_fma_tflops": fp32_fma_peak / 1e12},
         "solve_stats": {k: st[k] for k in ("restarts", "brick_marches", "march_rounds",
-                                            "exchanges", "accepted", "cell_solves", "n_bricks")},
+                                           "exchanges", "accepted", "cell_solves", "n_bricks")},
+        "per_point": {"accepted": st["accepted"] / pts, "cell_solves": st["cell_solves"] / pts,
+                      "marches_per_brick": st["brick_marches"] / st["n_bricks"]},
         "wall_ms_timed_region": wall_ms,
+        **others,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -565,7 +687,7 @@ def run_gpu(args):
 
 def _params(text):
     d = json.loads(text)
-    return {k: (float(v) if k in ("stride", "bucket") else int(v)) for k, v in d.items()}
+    return {k: (float(v) if k in ("stride", "bucket", "ahead") else int(v)) for k, v in d.items()}
 
 
 def main():
@@ -574,15 +696,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=N_GRID, help=argparse.SUPPRESS)
-    ap.add_argument("--part", default="all", choices=["all", "f32", "f64", "adjoint-f32", "adjoint-f64"],
-                    help="f32 / f64: only the timed solves of one dtype; adjoint-f32 / "
-                         "adjoint-f64: only the forward + adjoint pair (for profiling)")
+    ap.add_argument("--n", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--quick", action="store_true",
+                    help="only the headline workload (fp64 and fp32), no other configs")
+    ap.add_argument("--part", default="all",
+                    choices=["all", "c2-f32", "c2-f64", "c5-f32", "c5-f64", "adjoint-f32", "adjoint-f64"],
+                    help="c2-* / c5-*: only the timed solves of one workload and dtype; "
+                         "adjoint-*: only the forward + adjoint pair (for profiling)")
     ap.add_argument("--adjoint-n", type=int, default=512,
                     help="grid size of the adjoint workload of --part adjoint-*")
     ap.add_argument("--params", type=_params, default=None,
                     help="restart parameters as JSON (skips the autotuner), e.g. "
-                         "'{\"schedule\": 2, \"stride\": \"inf\"}'")
+                         "'{\"schedule\": 3, \"stride\": 1, \"ahead\": \"inf\"}'")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -73,7 +73,7 @@ typedef struct {
     int32_t record_tape;   /* 1: keep the upwind sets for fmm_adjoint           */
     double width;          /* width_band (Algorithm 5/12); 0 -> +inf (full march) */
     double stride;         /* restart stride delta_s in units of h (Algorithm 16);
-                              0 -> the GB300 default (16 for FMM_F32, 4 for
+                              0 -> the GB300 default (2 for FMM_F32, 1 for
                               FMM_F64; the paper suggests 2 for its CPU
                               cluster and tuning per platform, Sec. 5.5);
                               +inf allowed                                     */
@@ -102,8 +102,8 @@ typedef struct {
     int32_t max_lead;      /* continuous schedule: while bricks are queued or
                               marching, the bound stays within max_lead
                               strides of the smallest BAND value the last scan
-                              saw (a small front cannot run ahead); 0 -> 3;
-                              large values remove the limit                   */
+                              saw (a small front cannot run ahead); 0 -> no
+                              limit                                          */
     int32_t wait_limit_ms; /* every device-side wait (brick queue, bound
                               raise) gives up after this long without any
                               progress, sets an error bit and the call returns
@@ -118,6 +118,12 @@ typedef struct {
                               0 -> h.  The stride and the speed term are in
                               units of h, the bucket width in units of the
                               smallest cell size.  Batches need 0.          */
+    double ahead;          /* continuous schedule: a brick march accepts cells
+                              up to the bound plus ahead (units of h; +inf:
+                              the whole brick), and a brick whose only work
+                              is changed halo data waits until the bound
+                              reaches the smallest changed value; 0 -> +inf.
+                              The result does not depend on it.             */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */
@@ -242,13 +248,16 @@ fmm_status fmm_checkpoint_load(fmm_handle *hd, const void *host_buf, int64_t siz
 
 /*
  * fmm_create_batch -- a solver for n_grids independent grids of uneven sizes
- * that are reinitialised together (speed F = 1): the bricks of all grids are
- * packed into one brick array, and with the persistent schedule (the
- * default) every restart of Algorithm 16 is one launch that marches bricks
- * of all grids from one shared queue (phased: one launch per phase over one
+ * that are solved together (fmm_reinit_batch: level sets with speed F = 1;
+ * fmm_solve_batch: level sets or point sources, each grid with its own speed
+ * field or constant): the bricks of all grids are packed into one brick
+ * array, and with the continuous schedule (the default) the whole solve is
+ * one launch that marches bricks of all grids from one shared queue
+ * (persistent: one launch per restart; phased: one launch per phase over one
  * shared work list); a neighbour table stops data at the border of a grid.
  * The restart bound is common to all grids (Algorithm 16 is correct for any
- * bound; a grid whose front is done simply has no work).
+ * bound): a brick of any grid starts once the bound reaches its smallest
+ * BAND value, and a grid whose front is done simply has no work.
  *   dims : host, 3 * n_grids int64 (nx, ny, nz of every grid)
  *   h    : host, n_grids spacings
  *   cfg  : dtype, width, stride (in units of the smallest h), bucket,
@@ -268,6 +277,31 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
  */
 fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const *T_out,
                             uint8_t *const *tags_out);
+
+/*
+ * fmm_solve_batch -- solve every grid of a batch handle in one solve (the
+ * marches of all grids share one brick queue and one launch): each grid is
+ * either a two-sided reinitialisation of its level set (phi0[g] non-NULL,
+ * the rule of fmm_reinit_signed_distance) or a point-source problem
+ * (phi0[g] NULL: the n_src[g] cells (i, j, k) of src_ijk[g] get psi = 0,
+ * KNOWN_FIX, Algorithm 8), with its own speed: the device field speed[g]
+ * (x-fastest, dtype, finite, >= 0; 0 marks an obstacle cell as in
+ * fmm_create) or, where speed or speed[g] is NULL, the constant
+ * speed_const[g] (> 0; 1 when speed_const is NULL).
+ *   phi0, speed      : host arrays of n_grids device pointers (entries may be
+ *                      NULL), or NULL for all grids;
+ *   src_ijk, n_src   : host arrays of n_grids host pointers / counts (read only
+ *                      for grids without phi0; may be NULL when every grid has
+ *                      a level set);
+ *   speed_const      : host array of n_grids values, or NULL;
+ *   T_out, tags_out  : as fmm_reinit_batch.
+ * FMM_ERR_INVALID for a misaligned pointer, a source outside its grid, a
+ * grid with neither phi0 nor a source list, or a bad speed value.  (Batching
+ * is not part of the paper.)
+ */
+fmm_status fmm_solve_batch(fmm_handle *hd, const void *const *phi0, const int64_t *const *src_ijk,
+                           const int64_t *n_src, const void *const *speed, const double *speed_const,
+                           void *const *T_out, uint8_t *const *tags_out);
 
 /* fmm_get_stats -- statistics of the last solve (synchronises the stream). */
 fmm_status fmm_get_stats(const fmm_handle *hd, fmm_stats *out);
@@ -296,14 +330,16 @@ void fmm_destroy(fmm_handle *hd);
 /*
  * fmm_reinit_signed_distance_noalloc -- the same two-sided reinitialisation
  * as fmm_reinit_signed_distance with speed F = 1, for callers that cannot
- * allocate device memory when they solve: code running while a stream is
- * captured into a CUDA graph (where cudaMalloc is not allowed), processes
- * whose device memory belongs to a pool that forbids further allocations,
- * and loops that cannot afford an allocation.  The paper has no counterpart;
- * this is a packaging of the solve, not a different method.
+ * allocate device memory when they solve: processes whose device memory
+ * belongs to a pool or arena that forbids further driver allocations (a
+ * framework allocator that has reserved the device, an application with a
+ * fixed memory budget), and loops that cannot afford an allocation or an
+ * out-of-memory failure mid-run.  The paper has no counterpart; this is a
+ * packaging of the solve, not a different method.
  *   cfg      : host; nx, ny, nz, h, dtype, width, stride, bucket, ctas,
- *              max_restarts, timeout_s and stream are used; record_tape must
- *              be 0 (no adjoint); no handle is created.
+ *              schedule, exchange_passes, max_restarts, timeout_s and stream
+ *              are used and checked as fmm_create checks them; record_tape
+ *              must be 0 (no adjoint); no handle is created.
  *   phi0     : device (dtype), the level set; T_out: device (dtype), psi;
  *   tags_out : device uint8 tags or NULL.
  * No memory is allocated: the workspace is one file-scope device array of
@@ -311,13 +347,44 @@ void fmm_destroy(fmm_handle *hd);
  * exits.  Limit: at most 512 bricks of 8x8x8 cells (for example a 64^3 grid);
  * larger grids return FMM_ERR_INVALID.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  All calls on a device share the
+ * first call before any stream capture.  Later calls re-check the cached
+ * address (cudaPointerGetAttributes) and look it up again after a
+ * cudaDeviceReset.  The call synchronises cfg->stream: it reads the restart
+ * control block back between batches of restarts.  All calls on a device share the
  * array and each call clears what it needs; calls whose GPU work overlaps on
  * the same device (e.g. on two streams) race and give undefined results.
  * Errors are reported through fmm_last_error(NULL).
  */
 fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, const void *phi0, void *T_out,
                                               uint8_t *tags_out);
+
+/*
+ * fmm_selftest_fp64 -- diagnostics of the double-precision square root and
+ * division the fp64 march (Algorithm 11's root) and the adjoint use: for
+ * i < n, sqrt_out[i] = sqrt(a[i]) (a[i] >= 0) and div_out[i] = a[i] / b[i],
+ * computed by the library's own routines (float seeds refined by Newton steps
+ * in double; operands outside [1e-30, 1e30] in magnitude take CUDA's
+ * correctly rounded operation).  a, b, sqrt_out, div_out: device, n doubles
+ * each, caller-owned; enqueued on stream (cudaStream_t), asynchronous.
+ * FMM_ERR_INVALID for n < 0 or a NULL array, FMM_ERR_CUDA if the launch
+ * fails.  (Not part of the paper: it lets a test bound the routines' error.)
+ */
+fmm_status fmm_selftest_fp64(const double *a, const double *b, double *sqrt_out, double *div_out,
+                             int64_t n, void *stream);
+
+/*
+ * fmm_probe_fma_rate -- diagnostics: the device's fused multiply-add
+ * throughput in float (dtype FMM_F32) or double (FMM_F64), the arithmetic
+ * ceiling the march kernels are held to beside HBM bandwidth (on GB300 the
+ * double pipe, not memory, bounds the fp64 solve).  Runs iters steps of 8
+ * independent multiply-add chains per thread on 8 CTAs of 256 threads per SM
+ * of the current device (legacy default stream, a warm-up launch first),
+ * times the second launch with CUDA events and writes 2 * FMAs / second to
+ * *flops_per_s (host).  Synchronous.  FMM_ERR_INVALID for a NULL output,
+ * iters < 1 or another dtype; FMM_ERR_CUDA if a launch or event fails.
+ * (Not part of the paper.)
+ */
+fmm_status fmm_probe_fma_rate(int32_t dtype, int64_t iters, double *flops_per_s);
 
 #ifdef __cplusplus
 }

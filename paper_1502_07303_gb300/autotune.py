@@ -3,18 +3,20 @@
 The paper's only free parameter is the restart stride (Sec. 4.4, Sec. 5.1):
 it studies 0.5-3.5 h and infinity, suggests 2 h for its CPU cluster and
 advises experimenting on new platforms (Sec. 5.5).  On the GPU the stride,
-the restart schedule (persistent queue or phased passes), the bucket width
-of the local march, the number of exchange passes per restart and the
+the restart schedule (continuous, persistent queue or phased passes), the
+look-ahead of a brick march beyond the bound, the bucket width of the local
+march, the number of exchange passes per restart (phased schedule) and the
 number of CTAs of the march kernel all trade restarts against
-re-acceptance, so they are tuned together.  Many small fronts favour long
-strides (each restart ends in a tail where few bricks are left); one large
-front favours short ones (less re-acceptance).  The brick is fixed at
-8x8x8 (one warp per brick).
+re-acceptance, so they are tuned together.  The brick is 8x8x8 (one warp per
+brick, a 16-bit cell mask per lane); the CTA count sets how many bricks march
+at once.
 
 ``tune`` times every candidate on a representative problem with CUDA events
 and stores the fastest in a JSON cache keyed by (problem kind, dtype, size
-class = round(log2(points))); ``params_for`` reads it back (falling back to
-the library defaults).  Timing uses the CUDA library only.
+class = round(log2(points))); ``params_for`` reads it back (an empty dict, so
+the library defaults, when the class has no entry).  ``fmm.Solver`` and
+``fmm.Batch`` consult the cache for every parameter the caller leaves unset.
+Timing uses the CUDA library only.
 """
 from __future__ import annotations
 
@@ -27,22 +29,24 @@ import statistics
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                              "autotune.json")
 
-PARAMS = ("schedule", "stride", "bucket", "exchange_passes", "ctas", "max_lead")
+PARAMS = ("schedule", "stride", "bucket", "exchange_passes", "ctas", "max_lead", "ahead")
 
 SEARCH = {
     "schedule": [1, 2, 3],
-    "stride": [2.0, 4.0, 8.0, 16.0, 32.0, math.inf],
-    "bucket": [1.0, 2.0, 4.0, math.inf],
-    "exchange_passes": [0],
-    "ctas": [0],
+    "stride": [0.5, 1.0, 2.0, 4.0, 8.0, math.inf],
+    "bucket": [2.0, 3.0, 4.0, 6.0],
+    "exchange_passes": [1, 2],
+    "ctas": [0, 152 * 2, 152 * 4],
     "max_lead": [0],
+    "ahead": [math.inf, 8.0],
 }
 
-# A short list for a quick tune: the continuous schedule over strides (its
-# default lead, and without a lead limit at short strides), the persistent
-# one without restarts.
-QUICK = ([{"schedule": 3, "stride": s, "bucket": 4.0} for s in (4.0, 8.0, 16.0, 32.0)]
-         + [{"schedule": 3, "stride": s, "bucket": 4.0, "max_lead": 1 << 20} for s in (2.0, 4.0)]
+# A short list for a quick tune: the continuous schedule with a whole-brick
+# look-ahead over strides and bucket widths, at the full and at a reduced CTA
+# count, and the persistent schedule without restarts.
+QUICK = ([{"schedule": 3, "stride": s, "bucket": 4.0, "ahead": math.inf} for s in (0.5, 1.0, 2.0, 4.0)]
+         + [{"schedule": 3, "stride": 2.0, "bucket": b, "ahead": math.inf} for b in (3.0, 6.0)]
+         + [{"schedule": 3, "stride": 1.0, "bucket": 4.0, "ahead": math.inf, "ctas": 152 * 4}]
          + [{"schedule": 2, "stride": math.inf, "bucket": 4.0}])
 
 
@@ -88,6 +92,16 @@ def params_for(kind, dtype, n_points, path=None):
     if not entry:
         return {}
     return {k: entry[k] for k in PARAMS if k in entry}
+
+
+def merge(given, kind, dtype, n_points, path=None):
+    """The caller's parameters, completed from the cache: every tuned
+    parameter the caller left at its default (0) takes the cached value."""
+    out = dict(given)
+    for k, v in params_for(kind, dtype, n_points, path).items():
+        if not out.get(k):
+            out[k] = v
+    return out
 
 
 def candidates(search=None):
@@ -148,7 +162,7 @@ def tune(problem, dtype, kind=None, search=None, reps=2, path=None, save=True, l
     for params in candidates(search):
         try:
             with fmm.Solver(problem.shape, problem.h, dtype=dtype, speed=speed,
-                            sources=problem.sources, stream=stream, **params) as s:
+                            sources=problem.sources, stream=stream, tuned=False, **params) as s:
                 if phi is not None:
                     def run():
                         s.reinit(phi, T, None, want_tags=False)
@@ -171,6 +185,42 @@ def tune(problem, dtype, kind=None, search=None, reps=2, path=None, save=True, l
         entry["ms"] = best[1]
         entry["points"] = problem.n_points
         cache[key(kind, _dtype_name(dtype), problem.n_points)] = entry
+        save_cache(cache, path)
+    return best[0], best[1], table
+
+
+def tune_batch(problems, dtype, search=None, reps=2, path=None, save=True, stream=None):
+    """Time every candidate on a batch (a list of workloads.Problem with
+    phi0, reinitialised together through fmm.Batch) and store the fastest
+    under the kind "batch".  Returns (best_params, best_ms, table)."""
+    import torch
+
+    from . import fmm
+
+    phis = [torch.as_tensor(p.phi0, dtype=dtype, device="cuda").contiguous() for p in problems]
+    Ts = [torch.empty(p.shape, dtype=dtype, device="cuda") for p in problems]
+    pts = sum(p.n_points for p in problems)
+    table = []
+    for params in candidates(search):
+        try:
+            with fmm.Batch([p.shape for p in problems], [p.h for p in problems], dtype=dtype,
+                           stream=stream, tuned=False, **params) as b:
+                def run():
+                    b.reinit(phis, Ts, None, want_tags=False)
+                run()
+                ms = _time_call(torch, run, reps)
+        except fmm.FmmError:
+            ms = None
+        table.append((params, ms))
+    best = select_best(table)
+    if best is None:
+        return None, None, table
+    if save:
+        cache = load_cache(path)
+        entry = dict(best[0])
+        entry["ms"] = best[1]
+        entry["points"] = pts
+        cache[key("batch", _dtype_name(dtype), pts)] = entry
         save_cache(cache, path)
     return best[0], best[1], table
 

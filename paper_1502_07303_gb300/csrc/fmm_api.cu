@@ -47,6 +47,9 @@ struct fmm_handle {
     BatchGrid *h_grids = nullptr;      // pinned
     int *d_bgrid = nullptr;
     int *d_nbr = nullptr;
+    long long *d_bsrc = nullptr;       // batch sources, 4 per source (grid, i, j, k)
+    size_t bsrc_cap = 0;               // sources d_bsrc holds
+    bool batch_speed_const1 = true;    // the speed terms on the device are F = 1
     std::string err;
 };
 
@@ -79,7 +82,7 @@ fmm_status cuda_fail(fmm_handle *hd, cudaError_t e, const char *where)
 void free_state(fmm_handle *hd)
 {
     DeviceState &s = hd->st;
-    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.inbox, s.dirty,
+    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.inmin, s.inbox, s.dirty,
                     s.list[0], s.list[1], s.ctrl, hd->d_src, s.queue, s.queued};
     for (void *p : ptrs)
         if (p)
@@ -99,6 +102,10 @@ void free_state(fmm_handle *hd)
         cudaFree(hd->d_bgrid);
     if (hd->d_nbr)
         cudaFree(hd->d_nbr);
+    if (hd->d_bsrc)
+        cudaFree(hd->d_bsrc);
+    hd->d_bsrc = nullptr;
+    hd->bsrc_cap = 0;
     if (hd->h_grids)
         cudaFreeHost(hd->h_grids);
     hd->d_grids = nullptr;
@@ -231,6 +238,7 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
     FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.inmin, 0xff, (size_t)g.nbricks * 2 * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
     FMM_CUDA(hd, cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
@@ -421,6 +429,7 @@ std::vector<CkptSection> ckpt_sections(fmm_handle *hd)
         v.push_back({s.tape, cells});
     v.push_back({s.bmin, 2 * nb * hd->rsize});
     v.push_back({s.fresh, nb * kFaces * sizeof(unsigned long long)});
+    v.push_back({s.inmin, nb * 2 * sizeof(unsigned long long)});
     v.push_back({s.dirty, nb * sizeof(unsigned)});
     return v;
 }
@@ -474,8 +483,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
         return fail(nullptr, FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
-        cfg->bucket < 0.0 || std::isnan(cfg->bucket))
-        return fail(nullptr, FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
+        cfg->bucket < 0.0 || std::isnan(cfg->bucket) || cfg->ahead < 0.0 || std::isnan(cfg->ahead))
+        return fail(nullptr, FMM_ERR_INVALID, "width, stride, bucket and ahead must be >= 0");
     if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
         return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
     if (cfg->schedule < 0 || cfg->schedule > 3)
@@ -517,7 +526,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
                                                         : kScheduleContinuous;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
-    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();
+    p.ahead = (cfg->ahead > 0.0 ? cfg->ahead : default_ahead(cfg->dtype)) * p.h;
     p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
     p.hold = cfg->hold_queue != 0;
 
@@ -546,6 +556,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     ALLOC(s.bdelta, nb * hd->rsize);
     ALLOC(s.bmin, 2 * nb * hd->rsize);
     ALLOC(s.fresh, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.inmin, nb * 2 * sizeof(unsigned long long));
     ALLOC(s.inbox, nb * kFaces * sizeof(unsigned long long));
     ALLOC(s.dirty, nb * sizeof(unsigned));
     ALLOC(s.list[0], nb * sizeof(int));
@@ -736,7 +747,7 @@ fmm_status fmm_checkpoint_save(fmm_handle *hd, void *host_buf, int64_t capacity)
     CkptHeader hdr;
     memset(&hdr, 0, sizeof(hdr));
     memcpy(hdr.magic, kCkptMagic, sizeof(hdr.magic));
-    hdr.version = 1;
+    hdr.version = 2;
     hdr.dtype = hd->cfg.dtype;
     hdr.nx = hd->geom.nx;
     hdr.ny = hd->geom.ny;
@@ -770,7 +781,7 @@ fmm_status fmm_checkpoint_load(fmm_handle *hd, const void *host_buf, int64_t siz
     if (size < (int64_t)sizeof(hdr))
         return fail(hd, FMM_ERR_INVALID, "checkpoint too short");
     memcpy(&hdr, host_buf, sizeof(hdr));
-    if (memcmp(hdr.magic, kCkptMagic, sizeof(hdr.magic)) != 0 || hdr.version != 1)
+    if (memcmp(hdr.magic, kCkptMagic, sizeof(hdr.magic)) != 0 || hdr.version != 2)
         return fail(hd, FMM_ERR_INVALID, "not a checkpoint of this library");
     if (hdr.dtype != hd->cfg.dtype || hdr.nx != hd->geom.nx || hdr.ny != hd->geom.ny ||
         hdr.nz != hd->geom.nz || hdr.h != hd->params.h || hdr.hy != hd->params.hy ||
@@ -815,9 +826,9 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
         return fail(nullptr, FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
-        cfg->bucket < 0.0 || std::isnan(cfg->bucket) || cfg->exchange_passes < 0 ||
-        cfg->exchange_passes > 64)
-        return fail(nullptr, FMM_ERR_INVALID, "bad width, stride, bucket or exchange_passes");
+        cfg->bucket < 0.0 || std::isnan(cfg->bucket) || cfg->ahead < 0.0 || std::isnan(cfg->ahead) ||
+        cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
+        return fail(nullptr, FMM_ERR_INVALID, "bad width, stride, bucket, ahead or exchange_passes");
     if (cfg->record_tape)
         return fail(nullptr, FMM_ERR_INVALID, "batches keep no tape (record_tape must be 0)");
     if (cfg->hy != 0.0 || cfg->hz != 0.0)
@@ -841,6 +852,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
         G.nbz = (G.nz + kB - 1) / kB;
         G.brick0 = total;
         G.h = h[gi];
+        G.speed_const = 1.0;
         total += (long long)G.nbx * G.nby * G.nbz;
         hmin = h[gi] < hmin ? h[gi] : hmin;
     }
@@ -891,7 +903,8 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
                                                         : kScheduleContinuous;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
-    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();
+    p.ahead = (cfg->ahead > 0.0 ? cfg->ahead : default_ahead(cfg->dtype)) * p.h;
     p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
     p.hold = cfg->hold_queue != 0;
     p.spd_term = 0.0;
@@ -921,6 +934,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     ALLOC(s.bdelta, nb * hd->rsize);
     ALLOC(s.bmin, 2 * nb * hd->rsize);
     ALLOC(s.fresh, nb * kFaces * sizeof(unsigned long long));
+    ALLOC(s.inmin, nb * 2 * sizeof(unsigned long long));
     ALLOC(s.inbox, nb * kFaces * sizeof(unsigned long long));
     ALLOC(s.dirty, nb * sizeof(unsigned));
     ALLOC(s.list[0], nb * sizeof(int));
@@ -958,6 +972,111 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     return FMM_OK;
 }
 
+fmm_status fmm_solve_batch(fmm_handle *hd, const void *const *phi0, const int64_t *const *src_ijk,
+                           const int64_t *n_src, const void *const *speed, const double *speed_const,
+                           void *const *T_out, uint8_t *const *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "fmm_solve_batch needs a handle from fmm_create_batch");
+    if (!T_out)
+        return fail(hd, FMM_ERR_INVALID, "T_out must be an array of device pointers");
+    const int ng = hd->n_grids;
+    // per-grid problem: a level set, or point sources
+    long long total_src = 0;
+    bool any_speed = false;
+    for (int gi = 0; gi < ng; ++gi) {
+        const BatchGrid &G = hd->h_grids[gi];
+        const void *ph = phi0 ? phi0[gi] : nullptr;
+        const long long ns = (!ph && n_src) ? (long long)n_src[gi] : 0;
+        if (!T_out[gi] || !aligned16(T_out[gi]) || (ph && !aligned16(ph)))
+            return fail(hd, FMM_ERR_INVALID, "every phi0 and T_out must be 16-byte aligned");
+        if (!ph && (ns < 0 || (ns > 0 && (!src_ijk || !src_ijk[gi]))))
+            return fail(hd, FMM_ERR_INVALID, "a grid without phi0 needs its source list");
+        for (long long q = 0; q < ns; ++q) {
+            const int64_t *c = src_ijk[gi] + 3 * q;
+            if (c[0] < 0 || c[0] >= G.nx || c[1] < 0 || c[1] >= G.ny || c[2] < 0 || c[2] >= G.nz)
+                return fail(hd, FMM_ERR_INVALID, "source cell outside its grid");
+        }
+        const void *sp = speed ? speed[gi] : nullptr;
+        if (sp && !aligned16(sp))
+            return fail(hd, FMM_ERR_INVALID, "every speed must be 16-byte aligned");
+        const double sc = speed_const ? speed_const[gi] : 1.0;
+        if (!sp && !(sc > 0.0 && std::isfinite(sc)))
+            return fail(hd, FMM_ERR_INVALID, "speed_const must be finite and > 0 where speed is NULL");
+        any_speed = any_speed || sp || sc != 1.0;
+        total_src += ns;
+    }
+    cudaStream_t st = hd->stream;
+    const long long nb = hd->geom.nbricks;
+    // the source lists, flattened with their grid index
+    if (total_src > 0) {
+        std::vector<long long> flat((size_t)total_src * 4);
+        long long k = 0;
+        for (int gi = 0; gi < ng; ++gi) {
+            const long long ns = (!(phi0 && phi0[gi]) && n_src) ? (long long)n_src[gi] : 0;
+            hd->h_grids[gi].src0 = k;
+            hd->h_grids[gi].n_src = ns;
+            for (long long q = 0; q < ns; ++q, ++k) {
+                flat[(size_t)(4 * k)] = gi;
+                for (int a = 0; a < 3; ++a)
+                    flat[(size_t)(4 * k + 1 + a)] = src_ijk[gi][3 * q + a];
+            }
+        }
+        if ((size_t)total_src > hd->bsrc_cap) {
+            FMM_CUDA(hd, cudaStreamSynchronize(st));
+            if (hd->d_bsrc)
+                cudaFree(hd->d_bsrc);
+            hd->d_bsrc = nullptr;
+            hd->bsrc_cap = 0;
+            FMM_CUDA(hd, alloc(&hd->d_bsrc, (size_t)total_src * 4 * sizeof(long long)));
+            hd->bsrc_cap = (size_t)total_src;
+        }
+        FMM_CUDA(hd, cudaMemcpyAsync(hd->d_bsrc, flat.data(), flat.size() * sizeof(long long),
+                                     cudaMemcpyHostToDevice, st));
+        FMM_CUDA(hd, cudaStreamSynchronize(st));   // flat is a host temporary
+    }
+    for (int gi = 0; gi < ng; ++gi) {
+        BatchGrid &G = hd->h_grids[gi];
+        G.phi0 = phi0 ? phi0[gi] : nullptr;
+        G.T_out = T_out[gi];
+        G.tags_out = tags_out ? tags_out[gi] : nullptr;
+        G.speed = speed ? speed[gi] : nullptr;
+        G.speed_const = speed_const ? speed_const[gi] : 1.0;
+        if (total_src == 0)
+            G.src0 = G.n_src = 0;
+    }
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->d_grids, hd->h_grids, (size_t)ng * sizeof(BatchGrid),
+                                 cudaMemcpyHostToDevice, st));
+    long long pre = 1;
+    if (any_speed || !hd->batch_speed_const1) {
+        // speed terms and bucket widths of every grid; a bad speed value is
+        // reported before the solve starts
+        FMM_CUDA(hd, launch_reset_control(hd->st, st, hd->params.wait_ns, hd->params.hold));
+        FMM_CUDA(hd, launch_batch_speed(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
+        FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, hd->st.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA(hd, cudaStreamSynchronize(st));
+        hd->batch_speed_const1 = !any_speed;
+        pre += 2;
+        if (hd->h_ctrl->error & ERR_SPEED)
+            return fail(hd, FMM_ERR_INVALID, "speed values must be finite and >= 0");
+    }
+    FMM_CUDA(hd, launch_batch_init(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
+    if (total_src > 0) {
+        FMM_CUDA(hd, launch_batch_sources(hd->cfg.dtype, hd->d_grids, hd->d_bsrc, total_src, hd->st, st));
+        pre += 1;
+    }
+    hd->pre_launches = pre;
+    fmm_status rc = run_solve(hd, nullptr, nullptr);
+    if (rc != FMM_OK)
+        return rc;
+    FMM_CUDA(hd, launch_batch_output(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    hd->stats.kernel_launches += 1;
+    return FMM_OK;
+}
+
 fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const *T_out,
                             uint8_t *const *tags_out)
 {
@@ -967,26 +1086,10 @@ fmm_status fmm_reinit_batch(fmm_handle *hd, const void *const *phi0, void *const
         return fail(hd, FMM_ERR_STATE, "fmm_reinit_batch needs a handle from fmm_create_batch");
     if (!phi0 || !T_out)
         return fail(hd, FMM_ERR_INVALID, "phi0 and T_out must be arrays of device pointers");
-    for (int gi = 0; gi < hd->n_grids; ++gi) {
-        if (!phi0[gi] || !aligned16(phi0[gi]) || !T_out[gi] || !aligned16(T_out[gi]))
-            return fail(hd, FMM_ERR_INVALID, "every phi0 and T_out must be 16-byte aligned");
-        hd->h_grids[gi].phi0 = phi0[gi];
-        hd->h_grids[gi].T_out = T_out[gi];
-        hd->h_grids[gi].tags_out = tags_out ? tags_out[gi] : nullptr;
-    }
-    cudaStream_t st = hd->stream;
-    const long long nb = hd->geom.nbricks;
-    FMM_CUDA(hd, cudaMemcpyAsync(hd->d_grids, hd->h_grids, (size_t)hd->n_grids * sizeof(BatchGrid),
-                                 cudaMemcpyHostToDevice, st));
-    FMM_CUDA(hd, launch_batch_init(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
-    hd->pre_launches = 1;
-    fmm_status rc = run_solve(hd, nullptr, nullptr);
-    if (rc != FMM_OK)
-        return rc;
-    FMM_CUDA(hd, launch_batch_output(hd->cfg.dtype, hd->d_grids, hd->d_bgrid, nb, hd->st, st));
-    FMM_CUDA(hd, cudaStreamSynchronize(st));
-    hd->stats.kernel_launches += 1;
-    return FMM_OK;
+    for (int gi = 0; gi < hd->n_grids; ++gi)
+        if (!phi0[gi])
+            return fail(hd, FMM_ERR_INVALID, "every phi0 must be a 16-byte aligned device pointer");
+    return fmm_solve_batch(hd, phi0, nullptr, nullptr, nullptr, nullptr, T_out, tags_out);
 }
 
 fmm_status fmm_get_trace(const fmm_handle *hd, fmm_trace_entry *out, int64_t capacity,

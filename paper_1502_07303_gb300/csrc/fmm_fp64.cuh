@@ -6,8 +6,9 @@
 // single-precision seeds, move them between formats with integer operations
 // on the IEEE 754 bit patterns (binary32 / binary64: exponent biases 127 /
 // 1023, 23 / 52 fraction bits), and refine them with Newton steps in double.
-// Operands outside [1e-30, 1e30] in magnitude take the correctly rounded
-// operation instead.
+// Operands outside [1e-30, 1e30] in magnitude (for a division: a divisor
+// outside it, or a dividend above about 1e280, infinite or NaN) take the
+// correctly rounded operation instead.
 #pragma once
 
 #include <cstdint>
@@ -44,8 +45,10 @@ __device__ __forceinline__ double f64_of(float f)
     return __longlong_as_double((long long)((hi << 32) | (unsigned long long)(u << 29)));
 }
 
-// sqrt(v), v >= 0: float estimates y of sqrt(v) and rh of 1/(2 sqrt(v)),
-// one Newton step y + rh (v - y^2); relative error about 1e-14.
+// sqrt(v), v >= 0: float estimates y of sqrt(v) and rh of 1/(2 sqrt(v))
+// (relative errors eps <= 3.4e-7 and eta <= 3e-7: v truncated to a float,
+// rsqrtf), one Newton step y + rh (v - y^2); relative error eps^2/2 +
+// eta eps <= 1.6e-13 (measured worst over a log-uniform sweep: 3.4e-14).
 __device__ __forceinline__ double sqrt_fp64(double v)
 {
     const long long vb = __double_as_longlong(v);   // negative values sort below kF64Lo
@@ -58,11 +61,13 @@ __device__ __forceinline__ double sqrt_fp64(double v)
     return fma(rh, fma(-y, y, v), y);
 }
 
-// a / b: a float reciprocal of b refined by two Newton steps, then one
-// correction of the quotient; relative error about 1e-15.
+// a / b: a float reciprocal of b refined by two Newton steps (exact to
+// double rounding), then one correction of the quotient; a few ulp.
 __device__ __forceinline__ double div_fp64(double a, double b)
 {
-    if (!in_float_range(b))
+    // |a| at most 1e280 (bit pattern 0x7a0...): the Newton steps neither
+    // overflow nor meet an infinite or NaN dividend
+    if (!in_float_range(b) || (__double_as_longlong(a) & 0x7fffffffffffffffll) > 0x7a00000000000000ll)
         return a / b;
     double r = f64_of(1.0f / f32_of(b));
     r = r * fma(-b, r, 2.0);

@@ -2,6 +2,7 @@
 // libfmm_gb300.so.  Not part of the public ABI (that is include/fmm.h).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -100,6 +101,10 @@ struct SolveParams {
     int raise_at;       // continuous schedule: raise the bound when fewer
                         // bricks than this are queued or marching
     double max_lead;    // continuous schedule: lead of the bound in strides
+    double ahead;       // continuous schedule: a brick march accepts cells up
+                        // to bound + ahead (absolute units; +inf: the whole
+                        // brick), and a brick whose only work is halo changes
+                        // starts once the bound reaches their smallest value
     unsigned long long wait_ns;   // limit of a device wait without progress
     int hold;           // testing: keep one phantom brick pending
     int aniso;          // hy or hz differs from h
@@ -145,8 +150,14 @@ inline bool one_launch_schedule(int schedule)
 
 // Defaults of the restart parameters (units of h and of the bucket width),
 // measured on GB300 for 8^3 bricks.
-inline double default_stride(int dtype) { return dtype == 1 ? 4.0 : 16.0; }
+inline double default_stride(int dtype) { return dtype == 1 ? 1.0 : 2.0; }
 inline int default_passes(int dtype) { return dtype == 1 ? 1 : 2; }
+// continuous schedule: look-ahead of a brick march beyond the bound (units of
+// h; +inf: a brick marches to its end once the bound reaches its smallest
+// BAND or changed halo value) and the lead limit of the bound (strides;
+// +inf: none), measured on GB300 for 8^3 bricks
+inline double default_ahead(int) { return INFINITY; }
+inline double default_max_lead() { return INFINITY; }
 constexpr double kDefaultBucket = 4.0;
 
 // Device buffers owned by a handle (typed by the launchers).
@@ -158,6 +169,10 @@ struct DeviceState {
     uint8_t *tape;      // upwind set per cell or null
     void *bmin;         // 2 per brick: min |psi| of BAND cells per side
     unsigned long long *fresh;   // 6 per brick: changed-halo masks (live)
+    unsigned long long *inmin;   // 2 per brick (sides -1, +1): smallest value a
+                                 // neighbour flagged in the masks since the
+                                 // brick last took them (bits of a double;
+                                 // all ones: none recorded)
     unsigned long long *inbox;   // 6 per brick: masks taken by the last selection
     unsigned int *dirty;         // 1 per brick: has pending overlap changes
     int *list[2];       // work lists
@@ -174,9 +189,12 @@ struct BatchGrid {
     int nbx, nby, nbz;
     long long brick0;      // first brick of the grid in the packed brick array
     double h;
-    const void *phi0;      // caller's level set (x-fastest)
+    const void *phi0;      // caller's level set (x-fastest), or null: point sources
     void *T_out;           // caller's output psi (x-fastest)
     uint8_t *tags_out;     // caller's output tags or null
+    const void *speed;     // caller's speed field (x-fastest) or null: speed_const
+    double speed_const;
+    long long src0, n_src; // the grid's sources in the batch's source array
 };
 
 // Launchers (fmm_march.cu).  All enqueue on `stream`; `dtype` is 0 for float
@@ -219,6 +237,9 @@ cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgri
                               long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,
                                long long nbricks, const DeviceState &s, cudaStream_t stream);
+// src: 4 per source (grid, i, j, k)
+cudaError_t launch_batch_sources(int dtype, const BatchGrid *grids, const long long *src,
+                                 long long n_src, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bgrid,
                                 long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int which,

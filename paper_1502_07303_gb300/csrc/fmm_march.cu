@@ -39,6 +39,7 @@
 #include "fmm_internal.h"
 #include "fmm_queue.cuh"
 #include "fmm_fp64.cuh"
+#include "fmm_df.cuh"
 #include "fmm_lanes.cuh"
 
 #include <cfloat>
@@ -187,6 +188,18 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
         cswap(v[0], code[0], v[1], code[1]);
     }
     const real m = v[0];
+    if constexpr (sizeof(real) == 8) {
+        // double grids: the root in double-float arithmetic (fmm_df.cuh),
+        // unless the speed term is outside its range (an obstacle's +inf)
+        if (in_float_range(q)) {
+            double t = 0.0;
+            const int k = df_shifted_root(v[0], v[1], v[2], nd, q, t);
+            if (k == 0)
+                return INF;
+            set_out = (uint8_t)(code[0] | (k >= 2 ? code[1] : 0u) | (k == 3 ? code[2] : 0u));
+            return t;
+        }
+    }
     real d1 = nd >= 2 ? v[1] - m : (real)0;
     real d2 = nd >= 3 ? v[2] - m : (real)0;
 #pragma unroll 1
@@ -525,11 +538,14 @@ constexpr unsigned FULL = 0xffffffffu;
 template <typename real>
 struct WarpTile {
     real kv[kTile3];       // known values of the brick and its face halo
-    real tv[kB3];          // current |psi| of the brick's cells
-    uint8_t tp[kB3];       // upwind sets (tape)
-    uint16_t list[kB3];    // compacted cells to solve
+    alignas(16) real tv[kB3];          // current |psi| of the brick's cells
+    alignas(16) uint8_t tp[kB3];       // upwind sets (tape)
+    alignas(16) uint16_t list[kB3];    // compacted cells to solve (the tags
+                                       // while staging and writing back)
     unsigned improved[32]; // per owner lane: cells whose value dropped
 };
+static_assert(sizeof(WarpTile<float>) % 16 == 0 && sizeof(WarpTile<double>) % 16 == 0,
+              "every warp's tile starts on a 16-byte boundary");
 
 // Cells of lane l next to a halo cell flagged in the per-face masks F[6]
 // (face bit = u + 8 v with (u, v) the two in-face coordinates).
@@ -571,13 +587,14 @@ struct MarchStats {
 // compiler drops the set bookkeeping of Algorithm 11 altogether).  kAniso:
 // cells of unequal sizes (the weighted solve).  On
 // return, lanes 0..5 hold in notify_m / notify_nb the changed boundary cells
-// and the neighbour brick across face = lane (mode 1).
+// and the neighbour brick across face = lane (mode 1), and every lane holds in
+// notify_v[2] the smallest flagged value of each side (+inf: none).
 template <typename real, bool kHetero, int kMode, bool kFresh, bool kTape, bool kAniso>
 __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s, const SolveParams &p,
                                             double spd_const_term, WarpTile<real> &W, long long b,
                                             const unsigned long long *F_in, real bound0, real bound1,
                                             int lane, unsigned long long &notify_m,
-                                            long long &notify_nb, MarchStats &st)
+                                            long long &notify_nb, real *notify_v, MarchStats &st)
 {
     real *T = (real *)s.T;
     uint8_t *tag = s.tag;
@@ -594,18 +611,34 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
     const long long base = b * kB3;
 
     // ---- stage the brick ---------------------------------------------------
+    // The brick's values, tags (and tape) are contiguous: 16-byte loads copy
+    // them into shared memory (the tags into the list buffer, unused until
+    // the rounds), then every lane reads its own cells from there.
+    uint8_t *const stag = reinterpret_cast<uint8_t *>(W.list);
+    {
+        constexpr int kVecs = kB3 * (int)sizeof(real) / 16 / 32;   // 16-byte loads per lane
+        const uint4 *gv = reinterpret_cast<const uint4 *>(T + base);
+        uint4 *sv4 = reinterpret_cast<uint4 *>(W.tv);
+#pragma unroll
+        for (int j = 0; j < kVecs; ++j)
+            sv4[lane + 32 * j] = kFresh ? __ldcg(gv + lane + 32 * j) : gv[lane + 32 * j];
+        const uint4 *gt = reinterpret_cast<const uint4 *>(tag + base);
+        reinterpret_cast<uint4 *>(stag)[lane] = kFresh ? __ldcg(gt + lane) : gt[lane];
+        if (kTape) {
+            const uint4 *gp = reinterpret_cast<const uint4 *>(s.tape + base);
+            reinterpret_cast<uint4 *>(W.tp)[lane] = kFresh ? __ldcg(gp + lane) : gp[lane];
+        }
+    }
+    __syncwarp();
     unsigned band = 0, known = 0, fix = 0, out = 0, neg = 0;
     real r0 = INF, r1 = INF;   // lane minimum of the BAND cells of each side
 #pragma unroll 4
     for (int k = 0; k < 16; ++k) {
         const int c = lane + 32 * k;
-        const real v = kFresh ? __ldcg(T + base + c) : T[base + c];
-        const uint8_t t = kFresh ? __ldcg(tag + base + c) : tag[base + c];
+        const real v = W.tv[c];
+        const uint8_t t = stag[c];
         const uint8_t sv = t & ST_MASK;
-        W.tv[c] = v;
         W.kv[tile_of(c)] = sv >= ST_KNOWN ? v : INF;
-        if (kTape)
-            W.tp[c] = kFresh ? __ldcg(s.tape + base + c) : s.tape[base + c];
         band |= (unsigned)(sv == ST_BAND) << k;
         known |= (unsigned)(sv >= ST_KNOWN) << k;
         fix |= (unsigned)(sv == ST_FIX) << k;
@@ -815,7 +848,9 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
     // (Algorithm 11 uses only smaller known neighbours, and values only
     // decrease), so the exchange would change nothing there.
     unsigned long long fo0 = 0, fo1 = 0, fo2 = 0, fo3 = 0, fo4 = 0, fo5 = 0;
+    real fv0 = INF, fv1 = INF;   // smallest flagged value per side
     const unsigned chg = acc_any & known;
+    __syncwarp();   // the list buffer holds the tags again from here
 #pragma unroll 2
     for (int k = 0; k < 16; ++k) {
         const int c = lane + 32 * k;
@@ -833,27 +868,58 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             t = ST_FAR;
         if ((neg >> k) & 1u)
             t |= TG_NEG;
-        T[base + c] = v;
-        tag[base + c] = t;
-        if (kTape)
-            s.tape[base + c] = W.tp[c];
+        stag[c] = t;
         if (kMode == 1 && ((chg >> k) & 1u)) {
             const int y = lr + 4 * (k & 1), z = k >> 1;
             const int ti = tile_of(c);
-            if (lx == 0 && lt(v, W.kv[ti - 1]))
+            bool flagged = false;
+            if (lx == 0 && lt(v, W.kv[ti - 1])) {
                 fo0 |= 1ull << (y + 8 * z);
-            if (lx == 7 && lt(v, W.kv[ti + 1]))
+                flagged = true;
+            }
+            if (lx == 7 && lt(v, W.kv[ti + 1])) {
                 fo1 |= 1ull << (y + 8 * z);
-            if (y == 0 && lt(v, W.kv[ti - kTile]))
+                flagged = true;
+            }
+            if (y == 0 && lt(v, W.kv[ti - kTile])) {
                 fo2 |= 1ull << (lx + 8 * z);
-            if (y == 7 && lt(v, W.kv[ti + kTile]))
+                flagged = true;
+            }
+            if (y == 7 && lt(v, W.kv[ti + kTile])) {
                 fo3 |= 1ull << (lx + 8 * z);
-            if (z == 0 && lt(v, W.kv[ti - kTile * kTile]))
+                flagged = true;
+            }
+            if (z == 0 && lt(v, W.kv[ti - kTile * kTile])) {
                 fo4 |= 1ull << (lx + 8 * y);
-            if (z == 7 && lt(v, W.kv[ti + kTile * kTile]))
+                flagged = true;
+            }
+            if (z == 7 && lt(v, W.kv[ti + kTile * kTile])) {
                 fo5 |= 1ull << (lx + 8 * y);
+                flagged = true;
+            }
+            if (flagged) {
+                if ((neg >> k) & 1u)
+                    fv0 = vmin(fv0, v);
+                else
+                    fv1 = vmin(fv1, v);
+            }
         }
     }
+    // write back with 16-byte stores from shared memory
+    __syncwarp();
+    {
+        constexpr int kVecs = kB3 * (int)sizeof(real) / 16 / 32;
+        uint4 *gv = reinterpret_cast<uint4 *>(T + base);
+        const uint4 *sv4 = reinterpret_cast<const uint4 *>(W.tv);
+#pragma unroll
+        for (int j = 0; j < kVecs; ++j)
+            gv[lane + 32 * j] = sv4[lane + 32 * j];
+        reinterpret_cast<uint4 *>(tag + base)[lane] = reinterpret_cast<const uint4 *>(stag)[lane];
+        if (kTape)
+            reinterpret_cast<uint4 *>(s.tape + base)[lane] = reinterpret_cast<const uint4 *>(W.tp)[lane];
+    }
+    notify_v[0] = kMode == 1 ? warp_min(fv0) : INF;
+    notify_v[1] = kMode == 1 ? warp_min(fv1) : INF;
     if (lane == 0) {
         bmin[2 * b] = m0;
         bmin[2 * b + 1] = m1;
@@ -933,8 +999,9 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = kMode == 1 ? s.inbox[b * kFaces + f] : 0ull;
         unsigned long long m;
         long long nb;
+        real nv[2];
         march_brick<real, kHetero, kMode, false, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
-                                                 lane, m, nb, st);
+                                                 lane, m, nb, nv, st);
         if (kMode == 1 && m) {
             atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
             s.dirty[nb] = 1u;
@@ -999,8 +1066,9 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
+        real nv[2];
         march_brick<real, kHetero, 1, true, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
-                                            lane, m, nb, st);
+                                            lane, m, nb, nv, st);
         // publish the write-back before flagging anything
         __threadfence();
         __syncwarp();
@@ -1091,6 +1159,16 @@ __device__ __forceinline__ void queue_push_warp(Control *c, unsigned long long *
     }
 }
 
+// The smallest value neighbours flagged to brick side j (2 b + side) since it
+// last took its masks, +inf when none is recorded.
+constexpr unsigned long long kInminNone = ~0ull;
+template <typename real>
+__device__ __forceinline__ real inmin_value(const unsigned long long *inmin, long long j)
+{
+    const unsigned long long v = vloadu(inmin + j);
+    return v >= 0x7ff0000000000000ull ? inf_v<real>() : (real)__longlong_as_double((long long)v);
+}
+
 // One warp scans chunk ch of the per-brick minima for the bound (bd0, bd1).
 template <typename real>
 __device__ __forceinline__ void scan_chunk(const Geom &g, const DeviceState &s, int ch, real bd0,
@@ -1106,7 +1184,8 @@ __device__ __forceinline__ void scan_chunk(const Geom &g, const DeviceState &s, 
         const long long b = first + 32 * j + lane;
         bool sel = false;
         if (b < g.nbricks) {
-            const real m0 = __ldcg(bmin + 2 * b), m1 = __ldcg(bmin + 2 * b + 1);
+            const real m0 = vmin(__ldcg(bmin + 2 * b), inmin_value<real>(s.inmin, 2 * b));
+            const real m1 = vmin(__ldcg(bmin + 2 * b + 1), inmin_value<real>(s.inmin, 2 * b + 1));
             l0 = vmin(l0, m0);
             l1 = vmin(l1, m1);
             sel = (lt(m0, INF) && !lt(bd0, m0)) || (lt(m1, INF) && !lt(bd1, m1));
@@ -1308,13 +1387,22 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             continue;
         }
         const long long b = arg;
+        // forget the smallest flagged value, then take the masks: a value
+        // flagged in between is lost, and a brick with masks but no value
+        // counts as ready (below)
+        if (lane < 2)
+            atomicExch(&s.inmin[2 * b + lane], kInminNone);
+        __threadfence();
+        __syncwarp();
         unsigned long long mine = 0;
         if (lane < kFaces)
             mine = atomicExch(&s.fresh[b * kFaces + lane], 0ull);
         real bound0 = 0, bound1 = 0;
         if (lane == 0) {
-            bound0 = (real)vloadd(&ctrl->bound[0]);
-            bound1 = (real)vloadd(&ctrl->bound[1]);
+            // accept up to the bound plus the look-ahead, never beyond
+            // width_band (cells above it stay BAND, Algorithm 12)
+            bound0 = (real)fmin(vloadd(&ctrl->bound[0]) + p.ahead, p.width);
+            bound1 = (real)fmin(vloadd(&ctrl->bound[1]) + p.ahead, p.width);
         }
         __threadfence();
         bound0 = __shfl_sync(FULL, bound0, 0);
@@ -1325,15 +1413,28 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             F[f] = __shfl_sync(FULL, mine, f);
         unsigned long long m;
         long long nb;
+        real nv[2];
         march_brick<real, kHetero, 1, true, kTape, kAniso>(g, s, p, spd_const_term, W, b, F, bound0, bound1,
-                                            lane, m, nb, st);
+                                            lane, m, nb, nv, st);
         __threadfence();
         __syncwarp();
         if (m) {
+            // the value first, then the mask: a brick that sees the mask
+            // also sees a value at most this one (or none, see above)
+            const real INF = inf_v<real>();
+            if (lt(nv[0], INF))
+                atomicMin(&s.inmin[2 * nb], (unsigned long long)__double_as_longlong((double)nv[0]));
+            if (lt(nv[1], INF))
+                atomicMin(&s.inmin[2 * nb + 1], (unsigned long long)__double_as_longlong((double)nv[1]));
+            __threadfence();
             atomicOr(&s.fresh[nb * kFaces + (lane ^ 1)], m);
             st.exchanges += (unsigned long long)__popcll(m);
             __threadfence();
-            if (atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
+            // the neighbour starts now if what it was sent is at or below
+            // the bound; otherwise the scan of a later bound pushes it
+            const real cb0 = (real)vloadd(&ctrl->bound[0]), cb1 = (real)vloadd(&ctrl->bound[1]);
+            const bool ready = (lt(nv[0], INF) && !lt(cb0, nv[0])) || (lt(nv[1], INF) && !lt(cb1, nv[1]));
+            if (ready && atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
                 atomicAdd(&ctrl->pending, 1);
                 queue_push(ctrl, q, cap, nb);
             }
@@ -1343,15 +1444,23 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
             const real INF = inf_v<real>();
             const real m0 = bmin[2 * b], m1 = bmin[2 * b + 1];
             // end of the march: let others queue the brick again, and do it
-            // here if changes arrived meanwhile or the bound has risen above
+            // here if changes at or below the bound arrived meanwhile (or
+            // changes without a recorded value) or the bound has risen above
             // one of its BAND minima
             atomicExch(&s.queued[b], 0u);
             __threadfence();
-            bool again = false;
+            bool flagged = false;
 #pragma unroll
             for (int f = 0; f < kFaces; ++f)
-                again = again || (vload(&s.fresh[b * kFaces + f]) != 0ull);
+                flagged = flagged || (vload(&s.fresh[b * kFaces + f]) != 0ull);
             const real nb0 = (real)vloadd(&ctrl->bound[0]), nb1 = (real)vloadd(&ctrl->bound[1]);
+            bool again = false;
+            if (flagged) {
+                const unsigned long long i0 = vloadu(&s.inmin[2 * b]), i1 = vloadu(&s.inmin[2 * b + 1]);
+                const real v0 = inmin_value<real>(s.inmin, 2 * b), v1 = inmin_value<real>(s.inmin, 2 * b + 1);
+                again = (i0 == kInminNone && i1 == kInminNone) || (lt(v0, INF) && !lt(nb0, v0)) ||
+                        (lt(v1, INF) && !lt(nb1, v1));
+            }
             again = again || (lt(m0, INF) && !lt(nb0, m0)) || (lt(m1, INF) && !lt(nb1, m1));
             if (again && atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
                 atomicAdd(&ctrl->pending, 1);
@@ -1367,8 +1476,8 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 
 // Seed the queue of a restart: bricks with a BAND cell at or below the bound.
 template <typename real>
-__global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, unsigned *queued,
-                       unsigned long long *q)
+__global__ void k_seed(Geom g, const real *__restrict__ bmin, const unsigned long long *inmin,
+                       Control *ctrl, unsigned *queued, unsigned long long *q)
 {
     if (ctrl->done)
         return;
@@ -1392,7 +1501,8 @@ __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, uns
         const long long b = b0 + threadIdx.x;
         bool sel = false;
         if (b < g.nbricks) {
-            const double m0 = (double)bmin[2 * b], m1 = (double)bmin[2 * b + 1];
+            const double m0 = fmin((double)bmin[2 * b], inmin_value<double>(inmin, 2 * b));
+            const double m1 = fmin((double)bmin[2 * b + 1], inmin_value<double>(inmin, 2 * b + 1));
             sel = (m0 < CUDART_INF && m0 <= bd0) || (m1 < CUDART_INF && m1 <= bd1);
         }
         const unsigned ball = __ballot_sync(0xffffffffu, sel);
@@ -1417,8 +1527,8 @@ __global__ void k_seed(Geom g, const real *__restrict__ bmin, Control *ctrl, uns
 // ---------------------------------------------------------------------------
 
 template <typename real>
-__global__ void k_reduce(Geom g, const real *__restrict__ bmin, const unsigned *__restrict__ dirty,
-                         Control *ctrl)
+__global__ void k_reduce(Geom g, const real *__restrict__ bmin, const unsigned long long *inmin,
+                         const unsigned *__restrict__ dirty, Control *ctrl)
 {
     if (ctrl->done)
         return;
@@ -1428,8 +1538,8 @@ __global__ void k_reduce(Geom g, const real *__restrict__ bmin, const unsigned *
     unsigned cnt = 0;
     for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < g.nbricks;
          b += (long long)gridDim.x * blockDim.x) {
-        m0 = fmin(m0, (double)bmin[2 * b]);
-        m1 = fmin(m1, (double)bmin[2 * b + 1]);
+        m0 = fmin(m0, fmin((double)bmin[2 * b], inmin_value<double>(inmin, 2 * b)));
+        m1 = fmin(m1, fmin((double)bmin[2 * b + 1], inmin_value<double>(inmin, 2 * b + 1)));
         cnt += dirty[b] != 0u;
     }
     m0 = warp_min(m0);
@@ -1610,9 +1720,12 @@ __device__ __forceinline__ void batch_cell(const BatchGrid &G, long long b, int 
     k = bz * kB + (c >> 6);
 }
 
+// Algorithm 8 for every grid of a batch: a grid with a level set gets its
+// interface cells (reinit_cell), a grid of point sources starts all FAR
+// (k_batch_sources then fixes its sources).
 template <typename real>
-__global__ void k_batch_init_reinit(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
-                                    long long nbricks, real *T, uint8_t *tag)
+__global__ void k_batch_init(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
+                             long long nbricks, real *T, uint8_t *tag)
 {
     const long long n = nbricks * kB3;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -1626,6 +1739,11 @@ __global__ void k_batch_init_reinit(const BatchGrid *__restrict__ grids, const i
             tag[e] = TG_OUT | ST_FAR;
             continue;
         }
+        if (!G.phi0) {
+            T[e] = inf_v<real>();
+            tag[e] = ST_FAR;
+            continue;
+        }
         real Tv;
         uint8_t tg;
         reinit_cell<real>((const real *)G.phi0, G.nx, G.ny, G.nz, i, j, k, G.h, G.h, G.h, Tv, tg);
@@ -1634,20 +1752,62 @@ __global__ void k_batch_init_reinit(const BatchGrid *__restrict__ grids, const i
     }
 }
 
-// Speed term (h_g/F)^2 with F = 1 per cell (every grid has its own h) and the
-// bucket width h_g / sqrt(3) per brick.
+// The point sources of the batch: psi = 0, FIX (Algorithm 8).
 template <typename real>
-__global__ void k_batch_speed(const BatchGrid *__restrict__ grids, const int *__restrict__ bgrid,
-                              long long nbricks, real *spd, real *bdelta)
+__global__ void k_batch_sources(const BatchGrid *__restrict__ grids, const long long *__restrict__ src,
+                                long long n_src, real *T, uint8_t *tag)
 {
-    const long long n = nbricks * kB3;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long b = e >> 9;
-        const double h = grids[bgrid[b]].h;
-        spd[e] = speed_term((real)1, h);
-        if ((e & 511) == 0)
-            bdelta[b] = (real)(h / 1.7320508075688772);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n_src;
+         s += (long long)gridDim.x * blockDim.x) {
+        const BatchGrid &G = grids[src[4 * s]];
+        const int i = (int)src[4 * s + 1], j = (int)src[4 * s + 2], k = (int)src[4 * s + 3];
+        const long long b = G.brick0 + ((long long)(k >> 3) * G.nby + (j >> 3)) * G.nbx + (i >> 3);
+        const long long e = b * kB3 + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
+        T[e] = (real)0;
+        tag[e] = ST_FIX;
+    }
+}
+
+// Speed term (h_g/F)^2 of every cell of a batch (each grid its own h and its
+// own speed field or constant) and the bucket width h_g min(1/F) / sqrt(3)
+// of every brick; one CTA of 512 threads per brick, as k_load_speed.
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_batch_speed(const BatchGrid *__restrict__ grids,
+                                                          const int *__restrict__ bgrid,
+                                                          long long nbricks, real *spd, real *bdelta,
+                                                          Control *ctrl)
+{
+    __shared__ real red[kThreads / 32];
+    const int t = threadIdx.x;
+    for (long long b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        const BatchGrid &G = grids[bgrid[b]];
+        int i, j, k;
+        batch_cell(G, b, t, i, j, k);
+        const bool out = i >= G.nx || j >= G.ny || k >= G.nz;
+        real F = (real)G.speed_const;
+        if (G.speed && !out)
+            F = ((const real *)G.speed)[((long long)k * G.ny + j) * G.nx + i];
+        if (out)
+            F = (real)1;
+        if (!(F >= (real)0) || !(F < inf_v<real>()))
+            atomicOr(&ctrl->error, ERR_SPEED);
+        spd[b * kB3 + t] = speed_term(F, G.h);
+        real fm = out ? (real)0 : F;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+        if ((t & 31) == 0)
+            red[t >> 5] = fm;
+        __syncthreads();
+        if (t == 0) {
+            real mx = red[0];
+            for (int w = 1; w < kThreads / 32; ++w)
+                mx = fmax(mx, red[w]);
+            if (!(mx > (real)0))
+                mx = (real)1;
+            bdelta[b] = (real)(G.h / (1.7320508075688772 * (double)mx));
+        }
+        __syncthreads();
     }
 }
 
@@ -1750,10 +1910,10 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     const bool het = s.spd != nullptr, tape = s.tape != nullptr;
     const double sct = p.spd_term;
     const size_t sm = march_smem<real>();
-    k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.dirty, s.ctrl);
+    k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.inmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
     if (one_launch_schedule(p.schedule)) {
-        k_seed<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.ctrl, s.queued, s.queue);
+        k_seed<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.inmin, s.ctrl, s.queued, s.queue);
         if (trace)
             k_trace_seed<<<1, 1, 0, st>>>(s.ctrl, trace);
         if (ev)
@@ -1928,22 +2088,35 @@ cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgri
 {
     const int nb = grid_for(nbricks * kB3, 256, 152 * 32);
     if (dtype == 1)
-        k_batch_init_reinit<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (double *)s.T, s.tag);
+        k_batch_init<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (double *)s.T, s.tag);
     else
-        k_batch_init_reinit<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (float *)s.T, s.tag);
+        k_batch_init<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (float *)s.T, s.tag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sources(int dtype, const BatchGrid *grids, const long long *src,
+                                 long long n_src, const DeviceState &s, cudaStream_t st)
+{
+    if (n_src <= 0)
+        return cudaSuccess;
+    const int nb = grid_for(n_src, 256, 1024);
+    if (dtype == 1)
+        k_batch_sources<double><<<nb, 256, 0, st>>>(grids, src, n_src, (double *)s.T, s.tag);
+    else
+        k_batch_sources<float><<<nb, 256, 0, st>>>(grids, src, n_src, (float *)s.T, s.tag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,
                                long long nbricks, const DeviceState &s, cudaStream_t st)
 {
-    const int nb = grid_for(nbricks * kB3, 256, 152 * 32);
+    const int nb = grid_for(nbricks, 1, 152 * 8);
     if (dtype == 1)
-        k_batch_speed<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (double *)s.spd,
-                                                  (double *)s.bdelta);
+        k_batch_speed<double><<<nb, kThreads, 0, st>>>(grids, bgrid, nbricks, (double *)s.spd,
+                                                       (double *)s.bdelta, s.ctrl);
     else
-        k_batch_speed<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (float *)s.spd,
-                                                 (float *)s.bdelta);
+        k_batch_speed<float><<<nb, kThreads, 0, st>>>(grids, bgrid, nbricks, (float *)s.spd,
+                                                      (float *)s.bdelta, s.ctrl);
     return cudaGetLastError();
 }
 

@@ -1,22 +1,26 @@
 // fmm_noalloc.cu -- fmm_reinit_signed_distance_noalloc: the two-sided
 // reinitialisation without any memory allocation.
 //
-// Some callers cannot allocate device memory at solve time: code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not
-// allowed there), processes whose device memory is owned by a pool or
-// arena that forbids further driver allocations, and latency-bound loops
-// that must not pay for an allocation.  For them this entry point keeps all
-// of its workspace in one file-scope __device__ array of fixed size, which
-// the module loader reserves on every device that loads the library and
-// which stays reserved until the process exits.  The caller still passes
-// phi0 and the outputs.
+// Some callers cannot allocate device memory at solve time: processes whose
+// device memory is owned by a pool or arena that forbids further driver
+// allocations (a framework's caching allocator that has reserved the whole
+// device, an embedding application with a fixed memory budget), and
+// latency-bound loops that must not pay for an allocation or risk an
+// out-of-memory failure in the middle of a run.  For them this entry point
+// keeps all of its workspace in one file-scope __device__ array of fixed size,
+// which the module loader reserves on every device that loads the library and
+// which stays reserved until the process exits.  The caller still passes phi0
+// and the outputs.
 //
-// The host cannot use the array's name as a device address (in host code
-// it names a host-side stand-in), so on the first call on each device, with
-// that device current, the address is looked up with cudaGetSymbolAddress
-// and cached.  Every call on a device shares the same array, and the array
-// keeps the previous call's contents; everything the solve reads before
-// writing (exchange masks, dirty flags, the control block) is cleared at the
+// The host cannot use the array's name as a device address (in host code it
+// names a host-side stand-in), so on the first call on each device, with that
+// device current, the address is looked up with cudaGetSymbolAddress and
+// cached; that first call should come before any stream capture.  Later calls
+// check the cached address with cudaPointerGetAttributes (which allocates
+// nothing) and look it up again if the device's context was reset since.
+// Every call on a device shares the same array, and the array keeps the
+// previous call's contents; everything the solve reads before writing
+// (exchange masks, dirty flags, queue, the control block) is cleared at the
 // start of each call.  Two calls whose GPU work overlaps on the same device
 // (for example on two streams) race on the array.
 #include "fmm.h"
@@ -47,7 +51,8 @@ constexpr size_t kOffTag = align256(kOffT + kCells * sizeof(double));
 constexpr size_t kOffBdelta = align256(kOffTag + kCells);
 constexpr size_t kOffBmin = align256(kOffBdelta + kNoAllocMaxBricks * sizeof(double));
 constexpr size_t kOffFresh = align256(kOffBmin + 2 * kNoAllocMaxBricks * sizeof(double));
-constexpr size_t kOffInbox = align256(kOffFresh + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
+constexpr size_t kOffInmin = align256(kOffFresh + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
+constexpr size_t kOffInbox = align256(kOffInmin + 2 * kNoAllocMaxBricks * sizeof(unsigned long long));
 constexpr size_t kOffDirty = align256(kOffInbox + kFaces * kNoAllocMaxBricks * sizeof(unsigned long long));
 constexpr size_t kOffList0 = align256(kOffDirty + kNoAllocMaxBricks * sizeof(unsigned));
 constexpr size_t kOffList1 = align256(kOffList0 + kNoAllocMaxBricks * sizeof(int));
@@ -73,14 +78,25 @@ fmm_status cuda_error(cudaError_t e, const char *where)
     return error(FMM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this; make that call before any
-// stream capture).
+// Device address of the scratch on the current device, looked up on the
+// first call on a device (make that call before any stream capture) and
+// cached.  A cached address that no longer names device memory of this
+// device (the context was reset with cudaDeviceReset, which unloads and
+// reloads the module) is looked up again.
 fmm_status scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices)
         return error(FMM_ERR_INVALID, "device ordinal out of range for the no-allocation entry point");
     std::lock_guard<std::mutex> lock(g_mu);
+    if (g_addr[dev]) {
+        cudaPointerAttributes a;
+        const cudaError_t e = cudaPointerGetAttributes(&a, g_addr[dev]);
+        if (e != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev ||
+            a.devicePointer != g_addr[dev]) {
+            cudaGetLastError();   // clear the error of an unknown pointer
+            g_addr[dev] = nullptr;
+        }
+    }
     if (!g_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -109,8 +125,12 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     if (cfg->dtype != FMM_F32 && cfg->dtype != FMM_F64)
         return error(FMM_ERR_INVALID, "dtype must be FMM_F32 or FMM_F64");
     if (cfg->width < 0.0 || std::isnan(cfg->width) || cfg->stride < 0.0 || std::isnan(cfg->stride) ||
-        cfg->bucket < 0.0 || std::isnan(cfg->bucket))
-        return error(FMM_ERR_INVALID, "width, stride and bucket must be >= 0");
+        cfg->bucket < 0.0 || std::isnan(cfg->bucket) || cfg->ahead < 0.0 || std::isnan(cfg->ahead))
+        return error(FMM_ERR_INVALID, "width, stride, bucket and ahead must be >= 0");
+    if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
+        return error(FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
+    if (cfg->schedule < 0 || cfg->schedule > 3)
+        return error(FMM_ERR_INVALID, "schedule must be 0, 1, 2 or 3");
     if (cfg->record_tape)
         return error(FMM_ERR_INVALID, "the no-allocation entry point keeps no tape (record_tape must be 0)");
     if (!phi0 || ((uintptr_t)phi0 & 15u) || !T_out || ((uintptr_t)T_out & 15u))
@@ -147,6 +167,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     s.bdelta = base + kOffBdelta;
     s.bmin = base + kOffBmin;
     s.fresh = (unsigned long long *)(base + kOffFresh);
+    s.inmin = (unsigned long long *)(base + kOffInmin);
     s.inbox = (unsigned long long *)(base + kOffInbox);
     s.dirty = (unsigned *)(base + kOffDirty);
     s.list[0] = (int *)(base + kOffList0);
@@ -169,11 +190,10 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
                  : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
                                                         : kScheduleContinuous;
-    if (p.passes > 64)
-        return error(FMM_ERR_INVALID, "exchange_passes must be at most 64");
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
-    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : 3.0;
+    p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();
+    p.ahead = (cfg->ahead > 0.0 ? cfg->ahead : default_ahead(cfg->dtype)) * cfg->h;
     p.wait_ns = 1000000ull * (unsigned long long)(cfg->wait_limit_ms > 0 ? cfg->wait_limit_ms : 4000);
     p.hold = cfg->hold_queue != 0;
     p.raise_at = raise_threshold(s.march_ctas);
@@ -195,6 +215,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     // clear what the solve reads before it writes
     NA_CUDA(launch_reset_control(s, st, p.wait_ns, p.hold));
     NA_CUDA(cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
+    NA_CUDA(cudaMemsetAsync(s.inmin, 0xff, (size_t)g.nbricks * 2 * sizeof(unsigned long long), st));
     NA_CUDA(cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     NA_CUDA(cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
     NA_CUDA(cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));

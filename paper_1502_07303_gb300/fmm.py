@@ -13,6 +13,7 @@ import os
 import numpy as np
 import torch
 
+from . import autotune as _autotune
 from . import build as _build
 
 FMM_OK, FMM_ERR_INVALID, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE = range(6)
@@ -23,7 +24,7 @@ EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_dista
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
             "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch",
             "fmm_get_trace", "fmm_resume", "fmm_checkpoint_size", "fmm_checkpoint_save",
-            "fmm_checkpoint_load")
+            "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch")
 
 
 class FmmConfig(ctypes.Structure):
@@ -36,7 +37,7 @@ class FmmConfig(ctypes.Structure):
                 ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32),
-                ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("ahead", ctypes.c_double)]
 
 
 class FmmStats(ctypes.Structure):
@@ -95,15 +96,19 @@ def load(path: str | None = None):
     lib.fmm_create_batch.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(FmmConfig),
                                      ctypes.POINTER(vp)]
     lib.fmm_reinit_batch.argtypes = [vp, vp, vp, vp]
+    lib.fmm_solve_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.fmm_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     lib.fmm_resume.argtypes = [vp, i64, vp, vp]
     lib.fmm_checkpoint_size.argtypes = [vp, ctypes.POINTER(i64)]
     lib.fmm_checkpoint_save.argtypes = [vp, vp, i64]
     lib.fmm_checkpoint_load.argtypes = [vp, vp, i64]
+    lib.fmm_selftest_fp64.argtypes = [vp, vp, vp, vp, i64, vp]
+    lib.fmm_probe_fma_rate.argtypes = [ctypes.c_int32, i64, ctypes.POINTER(dbl)]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
               "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
               "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace", "fmm_resume",
-              "fmm_checkpoint_size", "fmm_checkpoint_save", "fmm_checkpoint_load"):
+              "fmm_checkpoint_size", "fmm_checkpoint_save", "fmm_checkpoint_load",
+              "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -154,12 +159,24 @@ class Solver:
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
                  max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
-                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, stream=None):
+                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, ahead=0.0, stream=None,
+                 tuned=True):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.code, self.dtype = _dtype_code(dtype)
         self.stream = stream
+        if tuned:
+            # parameters left at 0 take the autotuner's cached values (if any)
+            kind = "reinit" if sources is None else (
+                "sources" if speed is None or isinstance(speed, (int, float)) else "sources_speed")
+            t = _autotune.merge({"stride": stride, "bucket": bucket, "ctas": ctas,
+                                 "exchange_passes": exchange_passes, "schedule": schedule,
+                                 "max_lead": max_lead, "ahead": ahead},
+                                kind, self.dtype, nx * ny * nz)
+            stride, bucket, ctas = t["stride"], t["bucket"], t["ctas"]
+            exchange_passes, schedule = t["exchange_passes"], t["schedule"]
+            max_lead, ahead = t["max_lead"], t["ahead"]
         cfg = FmmConfig()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
         hx, hy, hz = _spacing(h)
@@ -178,6 +195,7 @@ class Solver:
         cfg.max_lead = int(min(max_lead, 1 << 30))
         cfg.wait_limit_ms = int(wait_limit_ms)
         cfg.hold_queue = int(hold_queue)
+        cfg.ahead = float(ahead)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)
@@ -316,10 +334,22 @@ class Batch:
 
     def __init__(self, shapes, hs, dtype=torch.float32, width=math.inf, stride=0.0, bucket=0.0,
                  exchange_passes=0, ctas=0, max_restarts=0, timeout_s=0, time_kernels=False,
-                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, stream=None):
+                 schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, ahead=0.0, stream=None,
+                 tuned=True):
         self.lib = load()
         self.code, self.dtype = _dtype_code(dtype)
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        if tuned:
+            # parameters left at 0 take the autotuner's cached values for a
+            # batch of this many points (if any)
+            pts = sum(a * b * c for a, b, c in self.shapes)
+            t = _autotune.merge({"stride": stride, "bucket": bucket, "ctas": ctas,
+                                 "exchange_passes": exchange_passes, "schedule": schedule,
+                                 "max_lead": max_lead, "ahead": ahead},
+                                "batch", self.dtype, pts)
+            stride, bucket, ctas = t["stride"], t["bucket"], t["ctas"]
+            exchange_passes, schedule = t["exchange_passes"], t["schedule"]
+            max_lead, ahead = t["max_lead"], t["ahead"]
         n = len(self.shapes)
         dims = np.ascontiguousarray([[sh[2], sh[1], sh[0]] for sh in self.shapes], dtype=np.int64)
         hh = np.ascontiguousarray(hs, dtype=np.float64)
@@ -339,6 +369,7 @@ class Batch:
         cfg.max_lead = int(min(max_lead, 1 << 30))
         cfg.wait_limit_ms = int(wait_limit_ms)
         cfg.hold_queue = int(hold_queue)
+        cfg.ahead = float(ahead)
         cfg.stream = _stream_handle(stream)
         handle = ctypes.c_void_p()
         rc = self.lib.fmm_create_batch(n, dims.ctypes.data, hh.ctypes.data, ctypes.byref(cfg),
@@ -364,6 +395,55 @@ class Batch:
             Go = (ctypes.c_void_p * n)(*[_dev_ptr(t, torch.uint8, sh, "tags_out").value
                                          for t, sh in zip(tags_outs, self.shapes)])
         rc = self.lib.fmm_reinit_batch(self.handle, P, To, Go)
+        if rc != FMM_OK:
+            raise FmmError(rc, self.lib.fmm_last_error(self.handle).decode())
+        return T_outs, tags_outs
+
+    def solve(self, phis=None, sources=None, speeds=None, T_outs=None, tags_outs=None,
+              want_tags=True):
+        """Solve every grid (fmm_solve_batch): grid g is a reinitialisation of
+        phis[g] (a CUDA tensor) or, where phis is None or phis[g] is None, a
+        point-source problem with the cells sources[g] ((k, 3) of (i, j, k));
+        speeds[g] is a CUDA tensor of F, a number, or None (F = 1)."""
+        n = len(self.shapes)
+        phis = [None] * n if phis is None else list(phis)
+        sources = [None] * n if sources is None else list(sources)
+        speeds = [None] * n if speeds is None else list(speeds)
+        if not (len(phis) == len(sources) == len(speeds) == n):
+            raise ValueError("one entry per grid")
+        if T_outs is None:
+            T_outs = [torch.empty(sh, dtype=self.dtype, device="cuda") for sh in self.shapes]
+        if tags_outs is None and want_tags:
+            tags_outs = [torch.empty(sh, dtype=torch.uint8, device="cuda") for sh in self.shapes]
+        P = (ctypes.c_void_p * n)(*[None if ph is None else _dev_ptr(ph, self.dtype, sh, "phi0").value
+                                    for ph, sh in zip(phis, self.shapes)])
+        keep = []
+        S = (ctypes.c_void_p * n)()
+        N = (ctypes.c_int64 * n)()
+        for g, (ph, src) in enumerate(zip(phis, sources)):
+            if ph is None:
+                if src is None:
+                    raise ValueError(f"grid {g} needs a level set or sources")
+                a = np.ascontiguousarray(np.asarray(src, dtype=np.int64).reshape(-1, 3))
+                keep.append(a)
+                S[g] = a.ctypes.data
+                N[g] = len(a)
+        V = (ctypes.c_void_p * n)()
+        C = (ctypes.c_double * n)()
+        for g, (sp, sh) in enumerate(zip(speeds, self.shapes)):
+            if sp is None or isinstance(sp, (int, float)):
+                C[g] = 1.0 if sp is None else float(sp)
+            else:
+                keep.append(sp)
+                V[g] = _dev_ptr(sp, self.dtype, sh, "speed").value
+                C[g] = 0.0
+        To = (ctypes.c_void_p * n)(*[_dev_ptr(t, self.dtype, sh, "T_out").value
+                                     for t, sh in zip(T_outs, self.shapes)])
+        Go = None
+        if tags_outs is not None:
+            Go = (ctypes.c_void_p * n)(*[_dev_ptr(t, torch.uint8, sh, "tags_out").value
+                                         for t, sh in zip(tags_outs, self.shapes)])
+        rc = self.lib.fmm_solve_batch(self.handle, P, S, N, V, C, To, Go)
         if rc != FMM_OK:
             raise FmmError(rc, self.lib.fmm_last_error(self.handle).decode())
         return T_outs, tags_outs
@@ -418,6 +498,19 @@ def reinit_noalloc(phi0, h, T_out, tags_out=None, width=math.inf, stride=0.0, bu
     if rc != FMM_OK:
         raise FmmError(rc, lib.fmm_last_error(None).decode())
     return T_out, tags_out
+
+
+def probe_fma_rate(dtype, iters=1 << 16):
+    """Measured fused multiply-add throughput of the current device in
+    float or double (flop/s, 2 per FMA): the arithmetic ceiling of the march
+    kernels next to HBM bandwidth."""
+    lib = load()
+    code, _ = _dtype_code(dtype)
+    out = ctypes.c_double(0.0)
+    rc = lib.fmm_probe_fma_rate(code, int(iters), ctypes.byref(out))
+    if rc != FMM_OK:
+        raise FmmError(rc, "fmm_probe_fma_rate failed")
+    return out.value
 
 
 class EikonalFn(torch.autograd.Function):

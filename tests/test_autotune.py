@@ -41,9 +41,19 @@ def test_candidate_list():
     assert all(set(c) <= set(autotune.PARAMS) for c in got)
 
 
+def test_unset_parameters_come_from_the_cache(tmp_path):
+    path = str(tmp_path / "tune.json")
+    n = 100 ** 3
+    autotune.save_cache({autotune.key("reinit", "f64", n): {"stride": 1.0, "bucket": 3.0,
+                                                             "ahead": math.inf, "ms": 2.0}}, path)
+    got = autotune.merge({"stride": 4.0, "bucket": 0.0}, "reinit", "float64", n, path=path)
+    assert got == {"stride": 4.0, "bucket": 3.0, "ahead": math.inf}
+    assert autotune.merge({"stride": 4.0}, "reinit", "float32", n, path=path) == {"stride": 4.0}
+
+
 def test_candidate_grid():
     c = list(autotune.candidates({"schedule": [2], "stride": [2.0, 8.0], "bucket": [1.0],
-                                  "exchange_passes": [1, 2]}))
+                                  "exchange_passes": [1, 2], "ctas": [0], "ahead": [math.inf]}))
     assert len(c) == 4 and all(set(x) == set(autotune.PARAMS) for x in c)
 
 
@@ -54,8 +64,8 @@ def test_tune_small_problem_on_gpu(oracle, tmp_path):
     from parity_util import compare
     p = wl.random_spheres(shape=(40, 40, 40), count=4, seed=21)
     path = str(tmp_path / "tune.json")
-    search = {"schedule": [1, 2], "stride": [4.0, 16.0, math.inf], "bucket": [1.0, 4.0],
-              "exchange_passes": [1, 2]}
+    search = {"schedule": [1, 3], "stride": [4.0, 16.0, math.inf], "bucket": [1.0, 4.0],
+              "exchange_passes": [1, 2], "ctas": [0], "ahead": [math.inf]}
     best, ms, table = autotune.tune(p, torch.float64, search=search, reps=1, path=path)
     assert best is not None and ms > 0 and len(table) == 24
     assert autotune.params_for("reinit", torch.float64, p.n_points, path=path) == best

@@ -44,7 +44,7 @@ def test_adjoint_matches_oracle_fp64(fmm, oracle, n, seed):
     d_ref, _ = oracle.adjoint(r, p.h, g, speed=p.speed)
     scale = np.max(np.abs(d_ref))
     assert scale > 0
-    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-11 * scale
+    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-12 * scale
     assert st["adjoint_iterations"] >= 1
 
 
@@ -55,7 +55,7 @@ def test_adjoint_dense_cotangent_fp64(fmm, oracle):
     _, _, d_gpu, _ = _gpu_adjoint(fmm, p, g)
     r = oracle.solve_sources(p.shape, p.sources, p.h, speed=p.speed, record=True)
     d_ref, _ = oracle.adjoint(r, p.h, g, speed=p.speed)
-    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-11 * np.max(np.abs(d_ref))
+    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-12 * np.max(np.abs(d_ref))
     # FIX cells (the sources) get no gradient
     for i, j, k in p.sources:
         assert d_gpu[k, j, i] == 0.0
@@ -96,17 +96,28 @@ def test_adjoint_two_sided_reinit_fp64(fmm, oracle):
         d_gpu = s.adjoint(torch.as_tensor(g, device="cuda")).cpu().numpy()
     r = oracle.solve_reinit(pr.phi0, pr.h, record=True)
     d_ref, _ = oracle.adjoint(r, pr.h, g)
-    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-11 * np.max(np.abs(d_ref))
+    assert np.max(np.abs(d_gpu - d_ref)) <= 1e-12 * np.max(np.abs(d_ref))
 
 
-def test_adjoint_fp32_close_to_oracle(fmm, oracle):
-    p, g = _problem(24, 3)
+@pytest.mark.parametrize("n,seed", [(24, 3), (33, 5)])
+def test_adjoint_fp32_cell_by_cell(fmm, oracle, n, seed):
+    """fp32 adjoint against the oracle's fp64 adjoint on the same (float)
+    speed field, cell by cell: |dL/ds_gpu - dL/ds_oracle| <= 1e-4 max|dL/ds|
+    at every cell.  The bound comes from the forward rounding: fp32 psi
+    carries a relative error of ~2^-24 psi, so each difference psi_p - psi_i
+    ~ h/F of the reverse sweep carries ~2^-24 psi F / h relative error
+    (~1e-6 at n = 33), and the sweep sums such terms along upwind paths of
+    up to ~n cells (measured worst: 1.2e-6 at n = 24, 1.1e-5 at n = 33)."""
+    p, g = _problem(n, seed)
     F32 = np.asarray(p.speed, np.float32)
     _, _, d_gpu, _ = _gpu_adjoint(fmm, p, g, dtype=torch.float32, speed=F32)
     r = oracle.solve_sources(p.shape, p.sources, p.h, speed=F32.astype(np.float64), record=True)
     d_ref, _ = oracle.adjoint(r, p.h, g, speed=F32.astype(np.float64))
-    err = np.linalg.norm(d_gpu - d_ref) / np.linalg.norm(d_ref)
-    assert err < 1e-3, err
+    scale = np.max(np.abs(d_ref))
+    worst = float(np.max(np.abs(d_gpu.astype(np.float64) - d_ref)))
+    assert worst <= 1e-4 * scale, (worst / scale)
+    # cells the oracle gives no gradient (FIX, unreached) get none
+    assert np.all(d_gpu[d_ref == 0] == 0)
 
 
 def test_adjoint_requires_tape(fmm):
@@ -128,7 +139,7 @@ def test_eikonal_autograd_function(fmm, oracle):
     r = oracle.solve_sources(p.shape, p.sources, p.h, speed=p.speed, record=True)
     d_ref, _ = oracle.adjoint(r, p.h, g, speed=p.speed)
     d = s0.grad.cpu().numpy()
-    assert np.max(np.abs(d - d_ref)) <= 1e-11 * np.max(np.abs(d_ref))
+    assert np.max(np.abs(d - d_ref)) <= 1e-12 * np.max(np.abs(d_ref))
     solver.close()
 
 

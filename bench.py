@@ -487,20 +487,23 @@ def roofline_hbm(r, pts, alg, kernel, dt, workload, peak, peak_kind):
 
 
 def roofline_alu(r, pts, kernel, dt, workload, fp64_peak, sms, sm_mhz):
-    """Arithmetic roofline of the dominant kernel.  fp64: double flops per
-    launch (ncu counts per point x points) over the launch time, against the
-    measured double FMA rate (fmm_probe_fma_rate).  fp32: issued warp
-    instructions per launch over the launch time, against the issue rate of
-    the SMs (4 schedulers x 1 warp instruction per clock x SMs x max clock)."""
+    """Arithmetic roofline of the dominant kernel.  fp64: double-pipe thread
+    instructions (DFMA + DADD + DMUL, ncu counts per point x points) per
+    launch over the launch time, against the measured double FMA instruction
+    rate (fmm_probe_fma_rate / 2: every one of them occupies the double pipe
+    like an FMA).  fp32: issued warp instructions per launch over the launch
+    time, against the issue rate of the SMs (4 schedulers x 1 warp
+    instruction per clock x SMs x max clock)."""
     launches = max(r["march_launches"], 1.0)
     avg_s = r["march_ms"] / launches / 1e3
     per_pt = ops_record(kernel, dt, workload)
     if dt == "f64":
-        peak = fp64_peak / 1e12 if fp64_peak else None
+        peak = fp64_peak / 2 / 1e12 if fp64_peak else None
         ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None
-        return {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+        return {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": peak,
+                "unit": "T double-pipe instructions/s",
                 "frac": (ach / peak) if (ach and peak) else None, "kernel": kernel,
-                "peak_kind": "measured (fmm_probe_fma_rate, double FMA chains)",
+                "peak_kind": "measured (fmm_probe_fma_rate, double FMA chains, FMAs/s)",
                 "ops_per_point": per_pt}
     peak = 4 * sms * sm_mhz * 1e6 / 1e12
     ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None

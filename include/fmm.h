@@ -359,6 +359,54 @@ fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, const void 
                                               uint8_t *tags_out);
 
 /*
+ * Domain decomposition across processes (Sec. 4.1 and Algorithms 13-16): a
+ * handle from fmm_create holds one rank's subdomain -- its slab of z layers
+ * plus the ghost layer it shares with each neighbouring rank (the overlap
+ * Xi_p of Sec. 4.1 is two layers wide: the rank's last layer and the
+ * neighbour's first) -- and the caller runs the loop of Algorithm 16: the
+ * global reductions (AllReduce MIN of the per-side minima, MAX of the
+ * replaced-cell counts) and the exchange of overlap layers between ranks.
+ *   fmm_dd_start     -- Algorithms 8 and 9 on the subdomain: the level set
+ *                       phi0 (device, dtype, x-fastest) or, when phi0 is
+ *                       NULL, the handle's point sources.  phi0 holds
+ *                       extra_lo (0 or 1) layers below the subdomain and
+ *                       extra_hi (0 or 1) above it, the neighbours' layers
+ *                       beyond the ghost layers, so that the interface cells
+ *                       of the ghost layers are those of the whole grid:
+ *                       nx * ny * (nz + extra_lo + extra_hi) values.
+ *   fmm_dd_minima    -- minval[2] (host): the smallest |psi| of a BAND cell
+ *                       per side (-1, +1), width_band when there is none
+ *                       (the local heap tops of Algorithm 16).
+ *   fmm_dd_march     -- Algorithm 12 up to bound[2] (host; clipped to
+ *                       width_band): every brick with a BAND cell at or below
+ *                       the bound marches, and bricks whose halo changed march
+ *                       again until none is left.
+ *   fmm_dd_get_layers -- the nl layers z0 .. z0 + nl - 1 of signed psi
+ *                       (x-fastest, nx * ny * nl values of the dtype, +inf
+ *                       for FAR cells) into out (device): the outgoing buffer
+ *                       of Algorithm 13 (every value; the receiver keeps only
+ *                       the improvements).
+ *   fmm_dd_integrate -- Algorithm 15 on the layers z0 .. z0 + nl - 1 from in
+ *                       (device, as fmm_dd_get_layers writes them): a value
+ *                       of smaller magnitude than the local one replaces it
+ *                       as a BAND cell of its side (the next fmm_dd_march
+ *                       accepts it if it is within the bound); FIX cells are
+ *                       kept; *n_replaced (host, may be NULL) receives the
+ *                       number of replaced cells (count_new of Algorithm 13,
+ *                       counted where the data arrive).
+ *   fmm_dd_finish    -- the subdomain's signed psi and tags (device arrays,
+ *                       as fmm_solve).
+ * All calls synchronise cfg->stream.  FMM_ERR_STATE before fmm_dd_start;
+ * FMM_ERR_INVALID for layers outside the grid or non-device buffers.
+ */
+fmm_status fmm_dd_start(fmm_handle *hd, const void *phi0, int64_t extra_lo, int64_t extra_hi);
+fmm_status fmm_dd_minima(fmm_handle *hd, double *minval);
+fmm_status fmm_dd_march(fmm_handle *hd, const double *bound);
+fmm_status fmm_dd_get_layers(fmm_handle *hd, int64_t z0, int64_t nl, void *out);
+fmm_status fmm_dd_integrate(fmm_handle *hd, int64_t z0, int64_t nl, const void *in, int64_t *n_replaced);
+fmm_status fmm_dd_finish(fmm_handle *hd, void *T_out, uint8_t *tags_out);
+
+/*
  * fmm_selftest_fp64 -- diagnostics of the double-precision square root and
  * division the fp64 march (Algorithm 11's root) and the adjoint use: for
  * i < n, sqrt_out[i] = sqrt(a[i]) (a[i] >= 0) and div_out[i] = a[i] / b[i],

@@ -29,8 +29,11 @@ def _nvcc():
 
 
 def _flags(extra=()):
+    # FMM_GB300_NVCC_EXTRA: additional nvcc arguments (e.g. -D overrides of
+    # the tuning macros in fmm_internal.h / fmm_march.cu)
+    env = os.environ.get("FMM_GB300_NVCC_EXTRA", "").split()
     return [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-            "-I", INCLUDE, "-I", CSRC, *extra]
+            "-I", INCLUDE, "-I", CSRC, *env, *extra]
 
 
 def _deps():

@@ -29,6 +29,7 @@
 #include "fmm_lanes.cuh"
 
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 namespace fmmgb {
@@ -36,6 +37,11 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kAdjWarps = 4;
+
+__device__ __forceinline__ unsigned long long vloadu(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
 
 template <typename real>
 __device__ __forceinline__ real nan_v();
@@ -54,8 +60,12 @@ __device__ __forceinline__ void brick_xyz(const Geom &g, long long b, int &bx, i
     bz = (int)(r / g.nby);
 }
 
+// mu = NaN (not done) on accepted cells, 0 elsewhere; dL/ds = 0; and per
+// brick the largest |psi| of a cell to do (top, the bits of a double; the
+// caller zeroes it first).  A warp's 32 cells lie in one brick.
 template <typename real>
-__global__ void k_adj_init(Geom g, const uint8_t *__restrict__ tag, real *mu, real *dlds)
+__global__ void k_adj_init(Geom g, const real *__restrict__ T, const uint8_t *__restrict__ tag, real *mu,
+                           real *dlds, unsigned long long *top)
 {
     const long long n = g.nbricks * kB3;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -64,9 +74,72 @@ __global__ void k_adj_init(Geom g, const uint8_t *__restrict__ tag, real *mu, re
         brick_xyz(g, e >> 9, bx, by, bz);
         const int c = (int)(e & 511);
         const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
-        mu[e] = accepted(tag[e]) ? nan_v<real>() : (real)0;
+        const bool acc = accepted(tag[e]);
+        mu[e] = acc ? nan_v<real>() : (real)0;
         if (i < g.nx && j < g.ny && k < g.nz)
             dlds[((long long)k * g.ny + j) * g.nx + i] = (real)0;
+        const unsigned long long tb =
+            acc ? (unsigned long long)__double_as_longlong((double)T[e]) : 0ull;
+        // the warp maximum of the 64-bit patterns: high words first
+        const unsigned hi = __reduce_max_sync(FULL, (unsigned)(tb >> 32));
+        const unsigned lo = __reduce_max_sync(FULL, (unsigned)(tb >> 32) == hi ? (unsigned)tb : 0u);
+        if ((threadIdx.x & 31) == 0 && (hi | lo))
+            atomicMax(&top[e >> 9], ((unsigned long long)hi << 32) | lo);
+    }
+}
+
+// The largest top over all bricks into *out.
+__global__ void k_adj_top_max(long long nbricks, const unsigned long long *__restrict__ top,
+                              unsigned long long *out)
+{
+    unsigned long long m = 0;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbricks;
+         b += (long long)gridDim.x * blockDim.x)
+        m = top[b] > m ? top[b] : m;
+    const unsigned hi = __reduce_max_sync(FULL, (unsigned)(m >> 32));
+    const unsigned lo = __reduce_max_sync(FULL, (unsigned)(m >> 32) == hi ? (unsigned)m : 0u);
+    if ((threadIdx.x & 31) == 0 && (hi | lo))
+        atomicMax(out, ((unsigned long long)hi << 32) | lo);
+}
+
+// Between levels: the previous launch ended with the queue empty, but warps
+// that found it empty took tickets; restart the ring's positions.
+__global__ void k_adj_level_reset(Control *c)
+{
+    c->q_head = 0ull;
+    c->q_tail = 0ull;
+    c->pending = 0;
+}
+
+// A level of the reverse sweep: push every brick whose top lies in
+// [lo, hi) (bit patterns of non-negative doubles; top 0 = nothing to do).
+__global__ void k_adj_seed_level(Geom g, const unsigned long long *__restrict__ top,
+                                 unsigned long long lo, unsigned long long hi, Control *ctrl,
+                                 unsigned *queued, unsigned long long *q)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long cap = (unsigned long long)g.nbricks;
+    for (long long b0 = blockIdx.x * (long long)blockDim.x; b0 < g.nbricks;
+         b0 += (long long)gridDim.x * blockDim.x) {
+        const long long b = b0 + threadIdx.x;
+        bool sel = false;
+        if (b < g.nbricks) {
+            const unsigned long long t = top[b];
+            sel = t != 0ull && t >= lo && t < hi && atomicCAS(&queued[b], 0u, 1u) == 0u;
+        }
+        const unsigned ball = __ballot_sync(FULL, sel);
+        if (ball == 0u)
+            continue;
+        unsigned long long basepos = 0;
+        if (lane == 0) {
+            atomicAdd(&ctrl->pending, __popc(ball));
+            basepos = atomicAdd(&ctrl->q_tail, (unsigned long long)__popc(ball));
+        }
+        basepos = __shfl_sync(FULL, basepos, 0);
+        if (sel) {
+            const unsigned long long t = basepos + __popc(ball & ((1u << lane) - 1u));
+            q[t % cap] = ((t & 0xffffffffull) << 32) | (unsigned long long)(b + 1);
+        }
     }
 }
 
@@ -98,24 +171,11 @@ __device__ __forceinline__ double adj_div(double a, double b) { return div_fp64(
 __device__ __forceinline__ float adj_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double adj_sqrt(double v) { return sqrt_fp64(v); }
 
-// Seed: every brick is queued once.
-__global__ void k_adj_seed(Geom g, Control *ctrl, unsigned *queued, unsigned long long *q)
-{
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < g.nbricks;
-         b += (long long)gridDim.x * blockDim.x) {
-        queued[b] = 1u;
-        q[b] = ((unsigned long long)(b & 0xffffffffll) << 32) | (unsigned long long)(b + 1);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctrl->q_tail = (unsigned long long)g.nbricks;
-        ctrl->pending = (int)g.nbricks;
-    }
-}
-
 template <typename real, bool kHetero, bool kAniso>
 __global__ void __launch_bounds__(kAdjWarps * 32)
     k_adj_persistent(Geom g, DeviceState s, const real *__restrict__ dLdT, real *dlds, real *mu_g,
-                     double h, double spd_const_term, double wy, double wz)
+                     unsigned long long *top, unsigned long long level, double h,
+                     double spd_const_term, double wy, double wz)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -295,6 +355,20 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             const int k = __ffs(mm) - 1;
             mu_g[base + lane + 32 * k] = W.mu[tb_of(lx, lr, k)];
         }
+        // the brick's new top: the largest |psi| of a cell still to do
+        {
+            unsigned long long tmax = 0ull;
+            for (unsigned mm = todo; mm; mm &= mm - 1u) {
+                const int k = __ffs(mm) - 1;
+                const unsigned long long tb =
+                    (unsigned long long)__double_as_longlong((double)W.T[tb_of(lx, lr, k)]);
+                tmax = tb > tmax ? tb : tmax;
+            }
+            const unsigned hi = __reduce_max_sync(FULL, (unsigned)(tmax >> 32));
+            const unsigned lo = __reduce_max_sync(FULL, (unsigned)(tmax >> 32) == hi ? (unsigned)tmax : 0u);
+            if (lane == 0)
+                top[b] = ((unsigned long long)hi << 32) | lo;
+        }
         __threadfence();
         face_done = __reduce_or_sync(FULL, face_done);
         if (lane < kFaces && ((face_done >> lane) & 1u)) {
@@ -306,7 +380,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                 const long long nb = ((long long)nbz * g.nby + nby) * g.nbx + nbx;
                 atomicExch(&s.dirty[nb], 1u);
                 __threadfence();
-                if (atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
+                // started only once the level reaches its top; a later level's
+                // seed starts it otherwise
+                if (vloadu(&top[nb]) >= level && atomicCAS(&s.queued[nb], 0u, 1u) == 0u) {
                     atomicAdd(&ctrl->pending, 1);
                     queue_push(ctrl, s.queue, cap, nb);
                 }
@@ -317,7 +393,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             // end of the pass: queue the brick again if a flag arrived meanwhile
             atomicExch(&s.queued[b], 0u);
             __threadfence();
-            if (vload((const int *)&s.dirty[b]) != 0 && atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
+            if (vload((const int *)&s.dirty[b]) != 0 && vloadu(&top[b]) >= level &&
+                atomicCAS(&s.queued[b], 0u, 1u) == 0u) {
                 atomicAdd(&ctrl->pending, 1);
                 queue_push(ctrl, s.queue, cap, b);
             }
@@ -351,7 +428,7 @@ size_t adj_smem() { return sizeof(AdjTile<real>) * kAdjWarps; }
 
 template <typename real>
 cudaError_t adj_persistent_launch(const Geom &g, const DeviceState &s, const AdjointArgs &a,
-                                  cudaStream_t st)
+                                  unsigned long long level, cudaStream_t st)
 {
     const size_t sm = adj_smem<real>();
     int dev = 0, sms = 0, per_sm = 0;
@@ -363,7 +440,8 @@ cudaError_t adj_persistent_launch(const Geom &g, const DeviceState &s, const Adj
                                                       kAdjWarps * 32, sm);
         const int ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         k_adj_persistent<real, het, an><<<ctas, kAdjWarps * 32, sm, st>>>(
-            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, a.h, a.spd_term, a.wy, a.wz);
+            g, s, (const real *)a.dLdT, (real *)a.dlds, (real *)a.mu, (unsigned long long *)a.top, level,
+            a.h, a.spd_term, a.wy, a.wz);
     };
     using Y = std::true_type;
     using N = std::false_type;
@@ -400,23 +478,60 @@ cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
                                 const AdjointArgs &a, cudaStream_t st)
 {
     const int nb = grid_cap(g.nbricks * kB3, 256, 152 * 32);
+    cudaMemsetAsync(a.top, 0, (size_t)g.nbricks * sizeof(unsigned long long), st);
     if (dtype == 1) {
         adj_configure<double>();
-        k_adj_init<double><<<nb, 256, 0, st>>>(g, s.tag, (double *)a.mu, (double *)a.dlds);
+        k_adj_init<double><<<nb, 256, 0, st>>>(g, (const double *)s.T, s.tag, (double *)a.mu,
+                                               (double *)a.dlds, (unsigned long long *)a.top);
     } else {
         adj_configure<float>();
-        k_adj_init<float><<<nb, 256, 0, st>>>(g, s.tag, (float *)a.mu, (float *)a.dlds);
+        k_adj_init<float><<<nb, 256, 0, st>>>(g, (const float *)s.T, s.tag, (float *)a.mu,
+                                              (float *)a.dlds, (unsigned long long *)a.top);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_persistent(int dtype, const Geom &g, const DeviceState &s,
-                                      const AdjointArgs &a, cudaStream_t st)
+cudaError_t adjoint_top_max(int, const Geom &g, const AdjointArgs &a, double *out, cudaStream_t st)
+{
+    // the control block's second minimum word serves as the scratch word
+    unsigned long long *w = &a.ctrl->minbits[1];
+    cudaMemsetAsync(w, 0, sizeof(unsigned long long), st);
+    k_adj_top_max<<<grid_cap(g.nbricks, 256, 1024), 256, 0, st>>>(g.nbricks,
+                                                                   (const unsigned long long *)a.top, w);
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, w, sizeof(v), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return e;
+    memcpy(out, &v, sizeof(v));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_levels(int dtype, const Geom &g, const DeviceState &s,
+                                  const AdjointArgs &a, double top_max, double step, int levels,
+                                  cudaStream_t st)
 {
     const int nb = grid_cap(g.nbricks, 256, 152 * 32);
-    k_adj_seed<<<nb, 256, 0, st>>>(g, s.ctrl, s.queued, s.queue);
-    return dtype == 1 ? adj_persistent_launch<double>(g, s, a, st)
-                      : adj_persistent_launch<float>(g, s, a, st);
+    auto bits = [](double v) {
+        unsigned long long b;
+        memcpy(&b, &v, sizeof(b));
+        return b;
+    };
+    for (int k = 0; k < levels; ++k) {
+        // level k: tops in [top_max - (k + 1) step, top_max - k step); the
+        // first level is open above, the last one reaches down to 0
+        const double lo_v = k == levels - 1 ? 0.0 : top_max - (double)(k + 1) * step;
+        const unsigned long long lo = bits(lo_v > 0.0 ? lo_v : 0.0);
+        const unsigned long long hi = k == 0 ? ~0ull : bits(top_max - (double)k * step);
+        k_adj_level_reset<<<1, 1, 0, st>>>(s.ctrl);
+        k_adj_seed_level<<<nb, 256, 0, st>>>(g, (const unsigned long long *)a.top, lo, hi, s.ctrl,
+                                             s.queued, s.queue);
+        const cudaError_t e = dtype == 1 ? adj_persistent_launch<double>(g, s, a, lo, st)
+                                         : adj_persistent_launch<float>(g, s, a, lo, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_pending(int dtype, const Geom &g, const AdjointArgs &a, unsigned *count,

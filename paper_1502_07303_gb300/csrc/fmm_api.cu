@@ -37,6 +37,10 @@ struct fmm_handle {
     std::vector<fmm_trace_entry> trace;
     void *adj_mu = nullptr;            // adjoint workspace (lambda / D per cell)
     unsigned *adj_count = nullptr;
+    void *adj_top = nullptr;           // per brick: largest |psi| still to do
+    unsigned *dd_count = nullptr;      // domain decomposition: replaced cells
+    unsigned *h_dd_count = nullptr;    // pinned
+    bool dd_started = false;
     // device copies of the caller's host arrays (x-fastest, allocated on
     // first use): inputs and psi / dL/ds, a second array, tags
     void *stage[2] = {nullptr, nullptr};
@@ -116,6 +120,15 @@ void free_state(fmm_handle *hd)
         cudaFree(hd->adj_mu);
     if (hd->adj_count)
         cudaFree(hd->adj_count);
+    if (hd->adj_top)
+        cudaFree(hd->adj_top);
+    hd->adj_top = nullptr;
+    if (hd->dd_count)
+        cudaFree(hd->dd_count);
+    if (hd->h_dd_count)
+        cudaFreeHost(hd->h_dd_count);
+    hd->dd_count = nullptr;
+    hd->h_dd_count = nullptr;
     hd->adj_mu = nullptr;
     hd->adj_count = nullptr;
     for (void *&p : hd->stage) {
@@ -646,6 +659,8 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
         FMM_CUDA(hd, alloc(&hd->adj_mu, (size_t)g.nbricks * kB3 * hd->rsize));
     if (!hd->adj_count)
         FMM_CUDA(hd, alloc(&hd->adj_count, sizeof(unsigned)));
+    if (!hd->adj_top)
+        FMM_CUDA(hd, alloc(&hd->adj_top, (size_t)g.nbricks * sizeof(unsigned long long)));
     const bool host_out = is_host(dL_dslowness);
     fmm_status r = device_input(hd, dL_dT, 0, &dL_dT);
     void *dlds = dL_dslowness;
@@ -662,13 +677,25 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     a.wy = hd->params.wy;
     a.wz = hd->params.wz;
     a.aniso = hd->params.aniso;
+    a.top = hd->adj_top;
+    a.ctrl = s.ctrl;
     // every cell becomes ready once its downwind neighbours have published;
     // one persistent launch processes bricks until none is queued
     hd->resumable = false;   // the adjoint reuses the control block and the flags
     FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, launch_adjoint_init(dt, g, s, a, st));
-    FMM_CUDA(hd, launch_adjoint_persistent(dt, g, s, a, st));
+    // levels of the reverse sweep, from the largest |psi| down (a brick
+    // starts when the level reaches the largest |psi| it still has to do)
+    double top_max = 0.0;
+    FMM_CUDA(hd, adjoint_top_max(dt, g, a, &top_max, st));
+    FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
+    const double step = kAdjointLevelStep * hd->params.h;
+    long long levels = top_max > 0.0 ? (long long)std::ceil(top_max / step) + 1 : 1;
+    if (levels > kAdjointMaxLevels)
+        levels = kAdjointMaxLevels;
+    FMM_CUDA(hd, launch_adjoint_levels(dt, g, s, a, top_max, top_max / (double)(levels > 1 ? levels - 1 : 1),
+                                       (int)levels, st));
     if (host_out)
         FMM_CUDA(hd, cudaMemcpyAsync(dL_dslowness, dlds, natural_cells(hd) * hd->rsize,
                                      cudaMemcpyDeviceToHost, st));
@@ -718,6 +745,144 @@ fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_
     const fmm_status r = run_restarts(hd, T_out, tags_out, 0);
     hd->params.max_restarts = keep;
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Domain decomposition (Sec. 4.1, Algorithms 13-16 across processes): the
+// handle's grid is one rank's subdomain with its ghost layers; the caller
+// runs the loop of Algorithm 16 and the exchanges between ranks.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+fmm_status dd_layers_ok(fmm_handle *hd, int64_t z0, int64_t nl, const void *buf)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "batch handles have no domain decomposition");
+    if (!hd->dd_started)
+        return fail(hd, FMM_ERR_STATE, "fmm_dd_start first");
+    if (nl < 1 || z0 < 0 || z0 + nl > hd->geom.nz)
+        return fail(hd, FMM_ERR_INVALID, "layers outside the grid");
+    if (!buf || !aligned16(buf) || is_host(buf))
+        return fail(hd, FMM_ERR_INVALID, "layer buffers must be 16-byte aligned device memory");
+    return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status fmm_dd_start(fmm_handle *hd, const void *phi0, int64_t extra_lo, int64_t extra_hi)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "batch handles have no domain decomposition");
+    if (phi0 && (!aligned16(phi0) || is_host(phi0)))
+        return fail(hd, FMM_ERR_INVALID, "phi0 must be 16-byte aligned device memory");
+    if (extra_lo < 0 || extra_lo > 1 || extra_hi < 0 || extra_hi > 1)
+        return fail(hd, FMM_ERR_INVALID, "extra_lo and extra_hi must be 0 or 1");
+    DeviceState &s = hd->st;
+    const Geom &g = hd->geom;
+    const int dt = hd->cfg.dtype;
+    cudaStream_t st = hd->stream;
+    if (!hd->dd_count)
+        FMM_CUDA(hd, alloc(&hd->dd_count, sizeof(unsigned)));
+    if (!hd->h_dd_count)
+        FMM_CUDA(hd, cudaMallocHost((void **)&hd->h_dd_count, sizeof(unsigned)));
+    if (phi0) {
+        FMM_CUDA(hd, launch_init_reinit(dt, g, s, hd->params, phi0, st, (int)extra_lo, (int)extra_hi));
+    } else {
+        FMM_CUDA(hd, launch_init_sources(dt, g, s, hd->d_src, hd->n_src, st));
+    }
+    hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
+    FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
+    FMM_CUDA(hd, cudaMemsetAsync(s.fresh, 0, (size_t)g.nbricks * kFaces * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.inmin, 0xff, (size_t)g.nbricks * 2 * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.dirty, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.queue, 0, (size_t)g.nbricks * sizeof(unsigned long long), st));
+    FMM_CUDA(hd, cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
+    FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    hd->dd_started = true;
+    return FMM_OK;
+}
+
+fmm_status fmm_dd_minima(fmm_handle *hd, double *minval)
+{
+    if (!hd || !minval)
+        return fail(hd, FMM_ERR_INVALID, "handle and minval must not be NULL");
+    if (!hd->dd_started)
+        return fail(hd, FMM_ERR_STATE, "fmm_dd_start first");
+    FMM_CUDA(hd, launch_minima(hd->cfg.dtype, hd->geom, hd->st, hd->stream));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, hd->st.ctrl, sizeof(Control), cudaMemcpyDeviceToHost,
+                                 hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    for (int sd = 0; sd < 2; ++sd) {
+        double v;
+        const unsigned long long b = hd->h_ctrl->minbits[sd];
+        memcpy(&v, &b, sizeof(v));
+        minval[sd] = v < hd->params.width ? v : hd->params.width;
+    }
+    return FMM_OK;
+}
+
+fmm_status fmm_dd_march(fmm_handle *hd, const double *bound)
+{
+    if (!hd || !bound)
+        return fail(hd, FMM_ERR_INVALID, "handle and bound must not be NULL");
+    if (!hd->dd_started)
+        return fail(hd, FMM_ERR_STATE, "fmm_dd_start first");
+    if (std::isnan(bound[0]) || std::isnan(bound[1]) || bound[0] < 0.0 || bound[1] < 0.0)
+        return fail(hd, FMM_ERR_INVALID, "bounds must be >= 0");
+    const double b0 = bound[0] < hd->params.width ? bound[0] : hd->params.width;
+    const double b1 = bound[1] < hd->params.width ? bound[1] : hd->params.width;
+    FMM_CUDA(hd, launch_march_to(hd->cfg.dtype, hd->geom, hd->st, hd->params, b0, b1, hd->stream));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, hd->st.ctrl, sizeof(Control), cudaMemcpyDeviceToHost,
+                                 hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    if (hd->h_ctrl->error & (ERR_SPIN | ERR_ROUNDS))
+        return fail(hd, FMM_ERR_TIMEOUT, "a march exceeded its round or wait limit");
+    return FMM_OK;
+}
+
+fmm_status fmm_dd_get_layers(fmm_handle *hd, int64_t z0, int64_t nl, void *out)
+{
+    const fmm_status r = dd_layers_ok(hd, z0, nl, out);
+    if (r != FMM_OK)
+        return r;
+    FMM_CUDA(hd, launch_layer_export(hd->cfg.dtype, hd->geom, hd->st, (int)z0, (int)nl, out, hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    return FMM_OK;
+}
+
+fmm_status fmm_dd_integrate(fmm_handle *hd, int64_t z0, int64_t nl, const void *in, int64_t *n_replaced)
+{
+    const fmm_status r = dd_layers_ok(hd, z0, nl, in);
+    if (r != FMM_OK)
+        return r;
+    FMM_CUDA(hd, cudaMemsetAsync(hd->dd_count, 0, sizeof(unsigned), hd->stream));
+    FMM_CUDA(hd, launch_layer_integrate(hd->cfg.dtype, hd->geom, hd->st, (int)z0, (int)nl, in,
+                                        hd->dd_count, hd->stream));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_dd_count, hd->dd_count, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    if (n_replaced)
+        *n_replaced = (int64_t)*hd->h_dd_count;
+    return FMM_OK;
+}
+
+fmm_status fmm_dd_finish(fmm_handle *hd, void *T_out, uint8_t *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!hd->dd_started)
+        return fail(hd, FMM_ERR_STATE, "fmm_dd_start first");
+    if (!T_out || !aligned16(T_out) || is_host(T_out) || (tags_out && is_host(tags_out)))
+        return fail(hd, FMM_ERR_INVALID, "T_out (and tags_out) must be device memory, T_out 16-byte aligned");
+    FMM_CUDA(hd, launch_output(hd->cfg.dtype, hd->geom, hd->st, T_out, tags_out, hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    return FMM_OK;
 }
 
 fmm_status fmm_checkpoint_size(fmm_handle *hd, int64_t *bytes)

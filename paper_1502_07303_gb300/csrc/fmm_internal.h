@@ -202,9 +202,11 @@ struct BatchGrid {
 cudaError_t launch_init_sources(int dtype, const Geom &g, const DeviceState &s,
                                 const long long *src_ijk, long long n_src,
                                 cudaStream_t stream);
+// phi0 holds zlo extra layers below the grid and zhi above it (a subdomain
+// of a decomposed grid); 0, 0 for a whole grid
 cudaError_t launch_init_reinit(int dtype, const Geom &g, const DeviceState &s,
                                const SolveParams &p, const void *phi0,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int zlo = 0, int zhi = 0);
 // h: the x cell size of the speed term (h/F)^2; hmin: the smallest cell size,
 // the unit of the bucket width
 cudaError_t launch_load_speed(int dtype, const Geom &g, const DeviceState &s,
@@ -244,13 +246,32 @@ cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bg
                                 long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_select(int dtype, const Geom &g, const DeviceState &s, int which,
                           cudaStream_t stream);
+// domain decomposition: overlap layers z0 .. z0 + nl - 1 (signed psi,
+// x-fastest), their integration (count: replaced cells, added), one march to
+// a given bound, and the per-side BAND minima (into Control::minbits)
+cudaError_t launch_layer_export(int dtype, const Geom &g, const DeviceState &s, int z0, int nl,
+                                void *out, cudaStream_t stream);
+cudaError_t launch_layer_integrate(int dtype, const Geom &g, const DeviceState &s, int z0, int nl,
+                                   const void *in, unsigned *count, cudaStream_t stream);
+cudaError_t launch_march_to(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
+                            double b0, double b1, cudaStream_t stream);
+cudaError_t launch_minima(int dtype, const Geom &g, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t stream);
 
-// Adjoint (fmm_adjoint.cu).
+// Adjoint (fmm_adjoint.cu).  The reverse sweep runs by levels of |psi| of
+// kAdjointLevelStep h each (at most kAdjointMaxLevels).
+#ifndef FMM_ADJ_STEP_H
+#define FMM_ADJ_STEP_H 4.0
+#endif
+constexpr double kAdjointLevelStep = FMM_ADJ_STEP_H;
+constexpr long long kAdjointMaxLevels = 4096;
 struct AdjointArgs {
     const void *dLdT;   // caller's dL/dpsi, x-fastest
     void *dlds;         // caller's dL/ds output, x-fastest
     void *mu;           // lambda / D per cell (brick layout), NaN until done
+    void *top;          // per brick: largest |psi| of a cell still to do
+                        // (bits of a non-negative value; 0: none left)
+    Control *ctrl;      // the handle's control block (levels: Control::bound[0])
     double h;
     double spd_term;    // (h/F)^2 of a constant speed
     double wy, wz;      // (h/hy)^2, (h/hz)^2 (1 on a cubic-cell grid)
@@ -258,9 +279,15 @@ struct AdjointArgs {
 };
 cudaError_t launch_adjoint_init(int dtype, const Geom &g, const DeviceState &s,
                                 const AdjointArgs &a, cudaStream_t stream);
-// mode 0: every brick; mode 1: the bricks of work list `which`
-cudaError_t launch_adjoint_persistent(int dtype, const Geom &g, const DeviceState &s,
-                                      const AdjointArgs &a, cudaStream_t st);
+// The reverse sweep by descending levels: level k starts the bricks whose
+// largest unfinished |psi| is at or above top_max - (k + 1) step (the last
+// level every brick), each level one persistent launch.
+cudaError_t launch_adjoint_levels(int dtype, const Geom &g, const DeviceState &s,
+                                  const AdjointArgs &a, double top_max, double step, int levels,
+                                  cudaStream_t st);
+// the largest per-brick top into *out (host, synchronous)
+cudaError_t adjoint_top_max(int dtype, const Geom &g, const AdjointArgs &a, double *out,
+                            cudaStream_t st);
 cudaError_t launch_adjoint_pending(int dtype, const Geom &g, const AdjointArgs &a,
                                    unsigned *count, cudaStream_t stream);
 

@@ -334,19 +334,32 @@ __device__ __forceinline__ double warp_min(double v)
 // Algorithm 8: interface initialisation, written directly in brick layout.
 // ---------------------------------------------------------------------------
 
-template <typename real>
-__global__ void k_init_sources(Geom g, real *T, uint8_t *tag)
+// The per-cell kernels below run one CTA of kInitThreads threads per brick
+// (grid-stride over bricks), so the brick coordinates are computed once per
+// brick, with 32-bit arithmetic (a grid has fewer than 2^31 bricks).
+constexpr int kInitThreads = 256;
+
+__device__ __forceinline__ void brick_xyz32(const Geom &g, int b, int &bx, int &by, int &bz)
 {
-    const long long n = g.nbricks * kB3;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
+    bx = b % g.nbx;
+    const int r = b / g.nbx;
+    by = r % g.nby;
+    bz = r / g.nby;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kInitThreads) k_init_sources(Geom g, real *T, uint8_t *tag)
+{
+    for (int b = blockIdx.x; b < (int)g.nbricks; b += gridDim.x) {
         int bx, by, bz;
-        brick_coords(g, e >> 9, bx, by, bz);
-        const int c = (int)(e & 511);
-        const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
-        const bool out = i >= g.nx || j >= g.ny || k >= g.nz;
-        T[e] = inf_v<real>();
-        tag[e] = out ? (uint8_t)(TG_OUT | ST_FAR) : (uint8_t)ST_FAR;
+        brick_xyz32(g, b, bx, by, bz);
+        const long long base = (long long)b * kB3;
+        for (int c = threadIdx.x; c < kB3; c += kInitThreads) {
+            const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
+            const bool out = i >= g.nx || j >= g.ny || k >= g.nz;
+            T[base + c] = inf_v<real>();
+            tag[base + c] = out ? (uint8_t)(TG_OUT | ST_FAR) : (uint8_t)ST_FAR;
+        }
     }
 }
 
@@ -380,23 +393,40 @@ __device__ __forceinline__ float crossing(float fc, float fq, double h)
     return (fc / (fc - fq)) * (float)h;
 }
 
+__device__ __forceinline__ bool nonneg(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) == 0ull || (b << 1) == 0ull;
+}
+__device__ __forceinline__ bool nonneg(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    return (b >> 31) == 0u || (b << 1) == 0u;
+}
+
 // Algorithm 8 for one cell (i, j, k) of an nx*ny*nz level set with cells of
 // size hx * hy * hz (the crossing distance of an axis is a fraction of that
-// axis's cell size).
+// axis's cell size).  The level set may extend zlo layers below z = 0 and zhi
+// layers above z = nz - 1 (phi points at layer 0): a subdomain of a
+// decomposed grid sees the layers beyond its ghost layers, so its interface
+// cells are those of the whole grid.
 template <typename real>
 __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx, int ny, int nz,
                                             int i, int j, int k, double hx, double hy, double hz,
-                                            real &Tv, uint8_t &tg)
+                                            real &Tv, uint8_t &tg, int zlo = 0, int zhi = 0)
 {
     const double hs[3] = {hx, hy, hz};
     const long long sx = 1, sy = nx, sz = (long long)nx * ny;
     const long long p = (long long)k * sz + (long long)j * sy + i;
     const real fc = phi[p];
-    const bool pos = fc >= (real)0;
+    // sign tests on the bit patterns (phi >= 0: sign bit clear, or -0): the
+    // FP64 pipe's comparisons would bound the whole pass for double grids
+    const bool pos = nonneg(fc);
     real d[3];
     bool any = false;
     const int co[3] = {i, j, k};
-    const int ext[3] = {nx, ny, nz};
+    const int lo[3] = {0, 0, -zlo};
+    const int ext[3] = {nx, ny, nz + zhi};
     const long long st[3] = {sx, sy, sz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -404,10 +434,10 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
 #pragma unroll
         for (int dir = -1; dir <= 1; dir += 2) {
             const int q = co[a] + dir;
-            if (q < 0 || q >= ext[a])
+            if (q < lo[a] || q >= ext[a])
                 continue;
             const real fq = phi[p + dir * st[a]];
-            if ((fq >= (real)0) == pos)
+            if (nonneg(fq) == pos)
                 continue;
             const real dist = crossing(fc, fq, hs[a]);
             if (dist < d[a])
@@ -436,26 +466,27 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
 }
 
 template <typename real>
-__global__ void k_init_reinit(Geom g, double hx, double hy, double hz,
-                              const real *__restrict__ phi, real *T, uint8_t *tag)
+__global__ void __launch_bounds__(kInitThreads) k_init_reinit(Geom g, double hx, double hy, double hz,
+                                                              const real *__restrict__ phi, real *T,
+                                                              uint8_t *tag, int zlo, int zhi)
 {
-    const long long n = g.nbricks * kB3;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (int b = blockIdx.x; b < (int)g.nbricks; b += gridDim.x) {
         int bx, by, bz;
-        brick_coords(g, e >> 9, bx, by, bz);
-        const int c = (int)(e & 511);
-        const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
-        if (i >= g.nx || j >= g.ny || k >= g.nz) {
-            T[e] = inf_v<real>();
-            tag[e] = TG_OUT | ST_FAR;
-            continue;
+        brick_xyz32(g, b, bx, by, bz);
+        const long long base = (long long)b * kB3;
+        for (int c = threadIdx.x; c < kB3; c += kInitThreads) {
+            const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
+            if (i >= g.nx || j >= g.ny || k >= g.nz) {
+                T[base + c] = inf_v<real>();
+                tag[base + c] = TG_OUT | ST_FAR;
+                continue;
+            }
+            real Tv;
+            uint8_t tg;
+            reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, hx, hy, hz, Tv, tg, zlo, zhi);
+            T[base + c] = Tv;
+            tag[base + c] = tg;
         }
-        real Tv;
-        uint8_t tg;
-        reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, hx, hy, hz, Tv, tg);
-        T[e] = Tv;
-        tag[e] = tg;
     }
 }
 
@@ -993,6 +1024,29 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
     }
     while (it < n) {
         const long long b = (kMode == 0) ? it : (long long)work_list[it];
+        if (kMode == 0) {
+            // Algorithm 9 only changes cells next to a FIX cell: a brick with
+            // no FIX cell in it or in its six neighbours keeps the state of
+            // Algorithm 8 and has no BAND cell (one 16-byte load of tags per
+            // lane and brick decides)
+            bool fixnear = false;
+#pragma unroll
+            for (int f = -1; f < kFaces; ++f) {
+                const long long q = f < 0 ? b : neighbour_brick(g, s.nbr, b, f);
+                if (q < 0)
+                    continue;
+                const uint4 t4 = reinterpret_cast<const uint4 *>(s.tag + q * kB3)[lane];
+                const unsigned w = (t4.x & (t4.x >> 1)) | (t4.y & (t4.y >> 1)) | (t4.z & (t4.z >> 1)) |
+                                   (t4.w & (t4.w >> 1));
+                fixnear = fixnear || (w & 0x01010101u) != 0u;   // a byte with status ST_FIX (3)
+            }
+            if (!__any_sync(FULL, fixnear)) {
+                if (lane < 2)
+                    ((real *)s.bmin)[2 * b + lane] = inf_v<real>();
+                it += (long long)gridDim.x * kMarchWarps;
+                continue;
+            }
+        }
         unsigned long long F[kFaces];
 #pragma unroll
         for (int f = 0; f < kFaces; ++f)
@@ -1674,31 +1728,119 @@ __global__ void k_reset_control(Control *c, unsigned long long wait_ns, int hold
     c->epoch = 0;
 }
 
-// Brick layout -> the caller's x-fastest arrays (signed psi, public tags).
+// Brick layout -> the caller's x-fastest arrays (signed psi, public tags);
+// one CTA per brick, each warp writing rows of 8 consecutive cells.
 template <typename real>
-__global__ void k_output(Geom g, const real *__restrict__ T, const uint8_t *__restrict__ tag,
-                         real *T_out, uint8_t *tags_out)
+__global__ void __launch_bounds__(kInitThreads) k_output(Geom g, const real *__restrict__ T,
+                                                         const uint8_t *__restrict__ tag, real *T_out,
+                                                         uint8_t *tags_out)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (int b = blockIdx.x; b < (int)g.nbricks; b += gridDim.x) {
+        int bx, by, bz;
+        brick_xyz32(g, b, bx, by, bz);
+        const long long base = (long long)b * kB3;
+        for (int c = threadIdx.x; c < kB3; c += kInitThreads) {
+            const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
+            if (i >= g.nx || j >= g.ny || k >= g.nz)
+                continue;
+            const long long p = ((long long)k * g.ny + j) * g.nx + i;
+            const long long e = base + c;
+            const real v = T[e];
+            const uint8_t tg = tag[e];
+            const uint8_t st = tg & ST_MASK;
+            real out = v;
+            if (st == ST_FAR)
+                out = inf_v<real>();
+            else if (tg & TG_NEG)
+                out = -v;
+            T_out[p] = out;
+            if (tags_out)
+                tags_out[p] = st;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Domain decomposition (Sec. 4.1, Algorithms 13-15): the grid of one rank is
+// its slab of z layers plus the ghost layers it shares with its neighbours;
+// the overlap layers are read out (signed psi, +inf for FAR cells) and the
+// neighbour's copy of them is integrated.
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void k_layer_export(Geom g, const real *__restrict__ T, const uint8_t *__restrict__ tag,
+                               int z0, int nl, real *out)
+{
+    const long long n = (long long)g.nx * g.ny * nl;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p % g.nx);
         const long long r = p / g.nx;
-        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        const int j = (int)(r % g.ny), k = z0 + (int)(r / g.ny);
         const long long b = ((long long)(k >> 3) * g.nby + (j >> 3)) * g.nbx + (i >> 3);
         const long long e = b * kB3 + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
-        const real v = T[e];
         const uint8_t tg = tag[e];
-        const uint8_t st = tg & ST_MASK;
-        real out = v;
-        if (st == ST_FAR)
-            out = inf_v<real>();
+        real v = T[e];
+        if ((tg & ST_MASK) == ST_FAR)
+            v = inf_v<real>();
         else if (tg & TG_NEG)
-            out = -v;
-        T_out[p] = out;
-        if (tags_out)
-            tags_out[p] = st;
+            v = -v;
+        out[p] = v;
     }
+}
+
+// Algorithm 15: a received value smaller in magnitude than the local one
+// replaces it; the cell becomes BAND of the received value's side, so the
+// next march accepts it if it is within the bound (KNOWN_OLD of Algorithm
+// 15, then taken from the heap) or keeps it tentative (BAND_OLD).  FIX
+// cells are never replaced.  count receives the number of replaced cells.
+template <typename real>
+__global__ void k_layer_integrate(Geom g, real *T, uint8_t *tag, real *bmin, int z0, int nl,
+                                  const real *__restrict__ in, unsigned *count)
+{
+    const long long n = (long long)g.nx * g.ny * nl;
+    unsigned c = 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % g.nx);
+        const long long r = p / g.nx;
+        const int j = (int)(r % g.ny), k = z0 + (int)(r / g.ny);
+        const long long b = ((long long)(k >> 3) * g.nby + (j >> 3)) * g.nbx + (i >> 3);
+        const long long e = b * kB3 + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
+        const real v = in[p];
+        const real a = v < (real)0 ? -v : v;
+        const uint8_t tg = tag[e];
+        if ((tg & ST_MASK) == ST_FIX || !(a < inf_v<real>()))
+            continue;
+        const bool far = (tg & ST_MASK) == ST_FAR;
+        if (!far && !lt(a, T[e]))
+            continue;
+        const bool neg = v < (real)0 || (v == (real)0 && (tg & TG_NEG));
+        T[e] = a;
+        tag[e] = (uint8_t)(ST_BAND | (neg ? TG_NEG : 0));
+        if constexpr (sizeof(real) == 8)
+            atomicMin((unsigned long long *)&bmin[2 * b + (neg ? 0 : 1)],
+                      (unsigned long long)__double_as_longlong(a));
+        else
+            atomicMin((unsigned *)&bmin[2 * b + (neg ? 0 : 1)], __float_as_uint(a));
+        ++c;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd(count, c);
+}
+
+// Set the bound of a march to a given level (both sides) and empty the queue.
+__global__ void k_set_bound(Control *c, double b0, double b1)
+{
+    c->bound[0] = b0;
+    c->bound[1] = b1;
+    c->done = 0;
+    c->q_head = 0ull;
+    c->q_tail = 0ull;
+    c->pending = 0;
+    c->minbits[0] = c->minbits[1] = 0x7ff0000000000000ull;
+    c->dirty_count = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -1711,10 +1853,11 @@ __global__ void k_output(Geom g, const real *__restrict__ T, const uint8_t *__re
 __device__ __forceinline__ void batch_cell(const BatchGrid &G, long long b, int c, int &i, int &j,
                                            int &k)
 {
-    const long long lb = b - G.brick0;
-    const int bx = (int)(lb % G.nbx);
-    const long long r = lb / G.nbx;
-    const int by = (int)(r % G.nby), bz = (int)(r / G.nby);
+    // a batch has fewer than 2^31 bricks: 32-bit arithmetic
+    const int lb = (int)(b - G.brick0);
+    const int bx = lb % G.nbx;
+    const int r = lb / G.nbx;
+    const int by = r % G.nby, bz = r / G.nby;
     i = bx * kB + (c & 7);
     j = by * kB + ((c >> 3) & 7);
     k = bz * kB + (c >> 6);
@@ -1991,7 +2134,7 @@ int configure_march()
 cudaError_t launch_init_sources(int dtype, const Geom &g, const DeviceState &s,
                                 const long long *src_ijk, long long n_src, cudaStream_t st)
 {
-    const int nb = grid_for(g.nbricks * kB3, 256, 152 * 32);
+    const int nb = grid_for(g.nbricks, 1, 152 * 16);
     if (dtype == 1) {
         k_init_sources<double><<<nb, 256, 0, st>>>(g, (double *)s.T, s.tag);
         if (n_src > 0)
@@ -2007,15 +2150,17 @@ cudaError_t launch_init_sources(int dtype, const Geom &g, const DeviceState &s,
 }
 
 cudaError_t launch_init_reinit(int dtype, const Geom &g, const DeviceState &s,
-                               const SolveParams &p, const void *phi0, cudaStream_t st)
+                               const SolveParams &p, const void *phi0, cudaStream_t st, int zlo,
+                               int zhi)
 {
-    const int nb = grid_for(g.nbricks * kB3, 256, 152 * 32);
+    const int nb = grid_for(g.nbricks, 1, 152 * 16);
+    const long long layer = (long long)g.nx * g.ny;
     if (dtype == 1)
-        k_init_reinit<double><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const double *)phi0,
-                                                  (double *)s.T, s.tag);
+        k_init_reinit<double><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const double *)phi0 + zlo * layer,
+                                                  (double *)s.T, s.tag, zlo, zhi);
     else
-        k_init_reinit<float><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const float *)phi0,
-                                                 (float *)s.T, s.tag);
+        k_init_reinit<float><<<nb, 256, 0, st>>>(g, p.h, p.hy, p.hz, (const float *)phi0 + zlo * layer,
+                                                 (float *)s.T, s.tag, zlo, zhi);
     return cudaGetLastError();
 }
 
@@ -2055,12 +2200,75 @@ cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t st, unsigned
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s, void *T_out,
                           uint8_t *tags_out, cudaStream_t st)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz;
-    const int nb = grid_for(n, 256, 152 * 32);
+    const int nb = grid_for(g.nbricks, 1, 152 * 16);
     if (dtype == 1)
-        k_output<double><<<nb, 256, 0, st>>>(g, (const double *)s.T, s.tag, (double *)T_out, tags_out);
+        k_output<double><<<nb, kInitThreads, 0, st>>>(g, (const double *)s.T, s.tag, (double *)T_out,
+                                                      tags_out);
     else
-        k_output<float><<<nb, 256, 0, st>>>(g, (const float *)s.T, s.tag, (float *)T_out, tags_out);
+        k_output<float><<<nb, kInitThreads, 0, st>>>(g, (const float *)s.T, s.tag, (float *)T_out,
+                                                     tags_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layer_export(int dtype, const Geom &g, const DeviceState &s, int z0, int nl,
+                                void *out, cudaStream_t st)
+{
+    const int nb = grid_for((long long)g.nx * g.ny * nl, 256, 152 * 32);
+    if (dtype == 1)
+        k_layer_export<double><<<nb, 256, 0, st>>>(g, (const double *)s.T, s.tag, z0, nl, (double *)out);
+    else
+        k_layer_export<float><<<nb, 256, 0, st>>>(g, (const float *)s.T, s.tag, z0, nl, (float *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layer_integrate(int dtype, const Geom &g, const DeviceState &s, int z0, int nl,
+                                   const void *in, unsigned *count, cudaStream_t st)
+{
+    const int nb = grid_for((long long)g.nx * g.ny * nl, 256, 152 * 32);
+    if (dtype == 1)
+        k_layer_integrate<double><<<nb, 256, 0, st>>>(g, (double *)s.T, s.tag, (double *)s.bmin, z0, nl,
+                                                      (const double *)in, count);
+    else
+        k_layer_integrate<float><<<nb, 256, 0, st>>>(g, (float *)s.T, s.tag, (float *)s.bmin, z0, nl,
+                                                     (const float *)in, count);
+    return cudaGetLastError();
+}
+
+// One march of Algorithm 12 to a given bound: every brick with a BAND cell
+// at or below it marches, and bricks whose halo changed march again, until
+// none is left (the persistent queue).
+cudaError_t launch_march_to(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
+                            double b0, double b1, cudaStream_t st)
+{
+    k_set_bound<<<1, 1, 0, st>>>(s.ctrl, b0, b1);
+    const int rb = grid_for(g.nbricks, 256, 4096);
+    const bool het = s.spd != nullptr, tape = s.tape != nullptr;
+    if (dtype == 1) {
+        k_seed<double><<<rb, 256, 0, st>>>(g, (const double *)s.bmin, s.inmin, s.ctrl, s.queued, s.queue);
+        with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
+            k_march_persistent<double, decltype(H)::value, decltype(P)::value, decltype(A)::value>
+                <<<s.march_ctas, kMarchWarps * 32, march_smem<double>(), st>>>(g, s, p, p.spd_term);
+        });
+    } else {
+        k_seed<float><<<rb, 256, 0, st>>>(g, (const float *)s.bmin, s.inmin, s.ctrl, s.queued, s.queue);
+        with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
+            k_march_persistent<float, decltype(H)::value, decltype(P)::value, decltype(A)::value>
+                <<<s.march_ctas, kMarchWarps * 32, march_smem<float>(), st>>>(g, s, p, p.spd_term);
+        });
+    }
+    return cudaGetLastError();
+}
+
+// The per-side BAND minima of the grid (Algorithm 16's local heap tops) into
+// the control block (minbits).
+cudaError_t launch_minima(int dtype, const Geom &g, const DeviceState &s, cudaStream_t st)
+{
+    k_set_bound<<<1, 1, 0, st>>>(s.ctrl, 0.0, 0.0);
+    const int rb = grid_for(g.nbricks, 256, 4096);
+    if (dtype == 1)
+        k_reduce<double><<<rb, 256, 0, st>>>(g, (const double *)s.bmin, s.inmin, s.dirty, s.ctrl);
+    else
+        k_reduce<float><<<rb, 256, 0, st>>>(g, (const float *)s.bmin, s.inmin, s.dirty, s.ctrl);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,9 @@ EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_dista
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
             "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch",
             "fmm_get_trace", "fmm_resume", "fmm_checkpoint_size", "fmm_checkpoint_save",
-            "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch")
+            "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch",
+            "fmm_dd_start", "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers",
+            "fmm_dd_integrate", "fmm_dd_finish")
 
 
 class FmmConfig(ctypes.Structure):
@@ -97,6 +99,12 @@ def load(path: str | None = None):
                                      ctypes.POINTER(vp)]
     lib.fmm_reinit_batch.argtypes = [vp, vp, vp, vp]
     lib.fmm_solve_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.fmm_dd_start.argtypes = [vp, vp, i64, i64]
+    lib.fmm_dd_minima.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.fmm_dd_march.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.fmm_dd_get_layers.argtypes = [vp, i64, i64, vp]
+    lib.fmm_dd_integrate.argtypes = [vp, i64, i64, vp, ctypes.POINTER(i64)]
+    lib.fmm_dd_finish.argtypes = [vp, vp, vp]
     lib.fmm_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     lib.fmm_resume.argtypes = [vp, i64, vp, vp]
     lib.fmm_checkpoint_size.argtypes = [vp, ctypes.POINTER(i64)]
@@ -108,7 +116,9 @@ def load(path: str | None = None):
               "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
               "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace", "fmm_resume",
               "fmm_checkpoint_size", "fmm_checkpoint_save", "fmm_checkpoint_load",
-              "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch"):
+              "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch", "fmm_dd_start",
+              "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers", "fmm_dd_integrate",
+              "fmm_dd_finish"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib

@@ -691,7 +691,7 @@ fmm_status fmm_adjoint(fmm_handle *hd, const void *dL_dT, void *dL_dslowness)
     FMM_CUDA(hd, adjoint_top_max(dt, g, a, &top_max, st));
     FMM_CUDA(hd, launch_reset_control(s, st, hd->params.wait_ns, hd->params.hold));
     const double step = kAdjointLevelStep * hd->params.h;
-    long long levels = top_max > 0.0 ? (long long)std::ceil(top_max / step) + 1 : 1;
+    long long levels = (top_max > 0.0 && step > 0.0) ? (long long)std::ceil(top_max / step) + 1 : 1;
     if (levels > kAdjointMaxLevels)
         levels = kAdjointMaxLevels;
     FMM_CUDA(hd, launch_adjoint_levels(dt, g, s, a, top_max, top_max / (double)(levels > 1 ? levels - 1 : 1),

@@ -142,7 +142,10 @@ constexpr int kMarchWarps = 4;   // bricks in flight per CTA of the march kernel
 // or marching (a fraction of the warps of the march launch).
 inline int raise_threshold(int march_ctas) { return march_ctas * kMarchWarps / FMM_RAISE_DIV; }
 // bricks one warp scans for the next bound (continuous schedule)
-constexpr int kScanChunk = 1024;
+#ifndef FMM_SCAN_CHUNK
+#define FMM_SCAN_CHUNK 1024
+#endif
+constexpr int kScanChunk = FMM_SCAN_CHUNK;
 inline bool one_launch_schedule(int schedule)
 {
     return schedule == kSchedulePersistent || schedule == kScheduleContinuous;
@@ -258,10 +261,13 @@ cudaError_t launch_march_to(int dtype, const Geom &g, const DeviceState &s, cons
 cudaError_t launch_minima(int dtype, const Geom &g, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t stream);
 
-// Adjoint (fmm_adjoint.cu).  The reverse sweep runs by levels of |psi| of
-// kAdjointLevelStep h each (at most kAdjointMaxLevels).
+// Adjoint (fmm_adjoint.cu).  The reverse sweep can run by levels of |psi|
+// of kAdjointLevelStep h each (at most kAdjointMaxLevels); 0 (the default)
+// runs it as one level.  Measured on GB300 (512^3 heterogeneous speed):
+// steps of 4-128 h cut brick passes from 7 to 3.7-6 per brick but were 2-60 %
+// slower, so one level it is.
 #ifndef FMM_ADJ_STEP_H
-#define FMM_ADJ_STEP_H 4.0
+#define FMM_ADJ_STEP_H 0.0
 #endif
 constexpr double kAdjointLevelStep = FMM_ADJ_STEP_H;
 constexpr long long kAdjointMaxLevels = 4096;

@@ -395,8 +395,9 @@ __device__ __forceinline__ float crossing(float fc, float fq, double h)
 
 __device__ __forceinline__ bool nonneg(double v)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) == 0ull || (b << 1) == 0ull;
+    // sign bit clear, or -0, tested on the high word (and the low word for -0)
+    const int hi = __double2hiint(v);
+    return hi >= 0 || (hi == (int)0x80000000 && __double2loint(v) == 0);
 }
 __device__ __forceinline__ bool nonneg(float v)
 {
@@ -428,27 +429,40 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
     const int lo[3] = {0, 0, -zlo};
     const int ext[3] = {nx, ny, nz + zhi};
     const long long st[3] = {sx, sy, sz};
+    // the six neighbours first, all loads in flight together (a neighbour
+    // outside the grid reads the cell itself, which never changes sign)
+    real fn[6];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        d[a] = inf_v<real>();
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int dir = -1; dir <= 1; dir += 2) {
+        for (int s = 0; s < 2; ++s) {
+            const int dir = s ? 1 : -1;
             const int q = co[a] + dir;
-            if (q < lo[a] || q >= ext[a])
-                continue;
-            const real fq = phi[p + dir * st[a]];
-            if (nonneg(fq) == pos)
-                continue;
-            const real dist = crossing(fc, fq, hs[a]);
-            if (dist < d[a])
-                d[a] = dist;
-            any = true;
+            const long long off = (q < lo[a] || q >= ext[a]) ? 0ll : (dir < 0 ? -st[a] : st[a]);
+            fn[2 * a + s] = phi[p + off];
         }
+    bool cross[6];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        cross[n] = nonneg(fn[n]) != pos;
+        any = any || cross[n];
     }
     if (!any) {
         Tv = inf_v<real>();
         tg = pos ? (uint8_t)ST_FAR : (uint8_t)(ST_FAR | TG_NEG);
         return;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = inf_v<real>();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (!cross[2 * a + s])
+                continue;
+            const real dist = crossing(fc, fn[2 * a + s], hs[a]);
+            if (dist < d[a])
+                d[a] = dist;
+        }
     }
     real inv = (real)0;
     bool zero = false;

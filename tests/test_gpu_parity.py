@@ -334,3 +334,23 @@ def test_tape_and_tape_free_kernels_agree(fmm, oracle, dt, schedule, hetero):
         T, G, ref, _ = run_reinit(fmm, oracle, q.phi0, q.h, dt, schedule=schedule,
                                   record_tape=tape)
         compare(T, G, ref, dt)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_reinit_degenerate_level_sets(fmm, oracle, dt):
+    """Level sets without a front (one sign everywhere: every cell stays FAR,
+    psi = +inf on either side as Algorithm 8 initialises it) and with exact
+    zeros (a zero cell is an interface cell with psi = 0, sign +,
+    Algorithm 8), against the oracle."""
+    shape = (11, 9, 14)
+    h = wl.spacing(shape)
+    for phi in (np.full(shape, 0.3), np.full(shape, -0.2)):
+        T, G, ref, _ = run_reinit(fmm, oracle, phi, h, dt)
+        assert np.all(G == 0)
+        assert np.all(T == np.inf)
+        compare(T, G, ref, dt)
+    x = (np.arange(shape[2]) + 0.5) * h
+    phi = np.broadcast_to(np.round((x - 7.5 * h) / h)[None, None, :] * h, shape).copy()  # zeros at i = 7
+    T, G, ref, _ = run_reinit(fmm, oracle, phi, h, dt)
+    assert np.all(T[:, :, 7] == 0) and np.all(G[:, :, 7] == 3)
+    compare(T, G, ref, dt)

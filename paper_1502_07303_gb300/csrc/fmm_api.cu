@@ -590,7 +590,7 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     e = cudaMallocHost((void **)&hd->h_ctrl, sizeof(Control));
     if (e != cudaSuccess)
         return bail(cuda_fail(hd, e, "cudaMallocHost"));
-    const int per_sm = march_blocks_per_sm(cfg->dtype);
+    const int per_sm = march_blocks_per_sm(cfg->dtype, cfg->record_tape != 0);
     s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
     hd->params.raise_at = raise_threshold(s.march_ctas);
     fmm_status rc = load_speed(hd, speed, speed_const);
@@ -1118,7 +1118,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
         return bail(cuda_fail(hd, e, "cudaMallocHost"));
     memcpy(hd->h_grids, grids.data(), (size_t)n_grids * sizeof(BatchGrid));
     s.nbr = hd->d_nbr;
-    const int per_sm = march_blocks_per_sm(cfg->dtype);
+    const int per_sm = march_blocks_per_sm(cfg->dtype, false);
     s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
     hd->params.raise_at = raise_threshold(s.march_ctas);
     e = cudaMemcpy(hd->d_nbr, nbr.data(), nb * kFaces * sizeof(int), cudaMemcpyHostToDevice);

@@ -237,7 +237,7 @@ cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream,
                                  unsigned long long wait_ns, int hold);
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);
-int march_blocks_per_sm(int dtype);
+int march_blocks_per_sm(int dtype, bool tape);
 cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgrid,
                               long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,

@@ -90,8 +90,10 @@ __device__ __forceinline__ long long neighbour_brick(const Geom &g, const int *n
 // ---------------------------------------------------------------------------
 // Algorithm 11 (Solve_Quadratic_Parallel) on a staged tile.
 //
-// kv holds the value of every KNOWN/FIX cell of the brick and its halo and
-// +inf elsewhere, so "G in KNOWN and |psi_n| < |psi_cell|" is "kv_n < Tc".
+// kv holds the value of every KNOWN/FIX cell of the brick and its halo, +inf
+// for an unknown halo cell and the marked (sign bit set) value of every other
+// brick cell, so "G in KNOWN and |psi_n| < |psi_cell|" is "kv_n < Tc" on the
+// unsigned bit patterns (klt).
 // The per-axis choice and the nested upwind sets (each time dropping the
 // largest psi_i) follow the algorithm.  Algorithm 11 keeps the smallest
 // causal root over the sets; going from the full set down, the first causal
@@ -115,6 +117,34 @@ __device__ __forceinline__ bool lt(double a, double b)
 __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ double vmin(double a, double b) { return lt(a, b) ? a : b; }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+
+// Tile entries of the march: a known value as it is, any other brick cell
+// with its sign bit set (the "not known" mark, see WarpTile).  Compared as
+// unsigned bit patterns, a marked entry orders above every value including
+// +inf, so the smaller of two neighbours is the known one and a marked
+// entry is never below a cell's value: Algorithm 11's "known and smaller"
+// test costs no decoding.
+__device__ __forceinline__ bool klt(double a, double b)
+{
+    return (unsigned long long)__double_as_longlong(a) < (unsigned long long)__double_as_longlong(b);
+}
+__device__ __forceinline__ bool klt(float a, float b) { return __float_as_uint(a) < __float_as_uint(b); }
+__device__ __forceinline__ double kmin(double a, double b) { return klt(a, b) ? a : b; }
+__device__ __forceinline__ float kmin(float a, float b)
+{
+    return __uint_as_float(umin(__float_as_uint(a), __float_as_uint(b)));
+}
+// mark / unmark (set / clear the sign bit, on the high word of a double)
+__device__ __forceinline__ double kmark(double v)
+{
+    return __hiloint2double(__double2hiint(v) | (int)0x80000000, __double2loint(v));
+}
+__device__ __forceinline__ float kmark(float v) { return __uint_as_float(__float_as_uint(v) | 0x80000000u); }
+__device__ __forceinline__ double kval(double v)
+{
+    return __hiloint2double(__double2hiint(v) & 0x7fffffff, __double2loint(v));
+}
+__device__ __forceinline__ float kval(float v) { return __uint_as_float(__float_as_uint(v) & 0x7fffffffu); }
 
 // Double square root without the FP64 pipe's slow conversions (fmm_fp64.cuh).
 __device__ __forceinline__ double vsqrt(double v) { return sqrt_fp64(v); }
@@ -165,10 +195,10 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
-        const real w = vmin(vm, vp);
-        const bool up = lt(w, Tc);
+        const real w = kmin(vm, vp);
+        const bool up = klt(w, Tc);
         v[a] = up ? w : INF;
-        code[a] = up ? (lt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
+        code[a] = up ? (klt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
         nd += up;
     }
     set_out = 0;
@@ -264,11 +294,11 @@ __device__ __forceinline__ real solve_cell_w(const real *kv, int ti, real Tc, re
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const real vm = kv[ti - off[a]], vp = kv[ti + off[a]];
-        const real mn = vmin(vm, vp);
-        const bool up = lt(mn, Tc);
+        const real mn = kmin(vm, vp);
+        const bool up = klt(mn, Tc);
         v[a] = up ? mn : INF;
         w[a] = up ? wax[a] : (real)0;
-        code[a] = up ? (lt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
+        code[a] = up ? (klt(vp, vm) ? 2u : 1u) << (2 * a) : 0u;   // dead without a tape
         nd += up;
     }
     set_out = 0;
@@ -574,23 +604,87 @@ __global__ void __launch_bounds__(kThreads) k_load_speed(Geom g, double h, doubl
 #ifndef FMM_MARCH_BLOCKS_F32
 #define FMM_MARCH_BLOCKS_F32 7
 #endif
-// Resident CTAs per SM the march kernels are compiled for (registers): the
-// fp64 tile (12 KB a warp) already limits fp64 to four.
-template <typename real>
-constexpr int march_min_blocks() { return sizeof(real) == 4 ? FMM_MARCH_BLOCKS_F32 : 4; }
+#ifndef FMM_MARCH_BLOCKS_F64
+#define FMM_MARCH_BLOCKS_F64 5
+#endif
+#ifndef FMM_MARCH_BLOCKS_F64_TAPE
+#define FMM_MARCH_BLOCKS_F64_TAPE 5
+#endif
+// Resident CTAs per SM the march kernels are compiled for (registers); the
+// warp tiles (5.1 / 5.6 KB in float, 9.0 / 9.5 KB in double, without / with
+// the tape) allow these as well.  Measured on the 1024^3 sphere: fp64 with
+// 4 / 5 / 6 CTAs 261 / 236 / 242 ms (six leave 80 registers and spill),
+// fp32 with 6 / 7 / 8 CTAs 122 / 115 / 115 ms (eight slow the 256^3 case).
+template <typename real, bool kTape>
+constexpr int march_min_blocks()
+{
+    return sizeof(real) == 4 ? FMM_MARCH_BLOCKS_F32 : (kTape ? FMM_MARCH_BLOCKS_F64_TAPE : FMM_MARCH_BLOCKS_F64);
+}
 constexpr unsigned FULL = 0xffffffffu;
 
-template <typename real>
+// The brick and its face halo in one 10^3 tile (x fastest), shifted by one
+// entry so that every row of 8 brick cells starts on a 16-byte boundary in
+// double and an 8-byte boundary in float: kMT0 is the tile index of brick
+// cell (0, 0, 0), kMH0 that of halo position (0, 0, 0).  A brick cell holds
+// its current |psi|, with the sign bit set unless the cell is KNOWN or FIX; a
+// halo cell holds the neighbour's known value or +inf.  One array for the
+// known values and the current values keeps the fp64 tile at 9.5 KB a warp,
+// which lets five CTAs of four warps share an SM.
+constexpr int kMH0 = 1;
+constexpr int kMT0 = kMH0 + 1 + kTile + kTile * kTile;
+constexpr int kMTile = kMH0 + kTile3 + 1;
+
+__device__ __forceinline__ int mt_of(int c)
+{
+    return kMT0 + (c & 7) + kTile * ((c >> 3) & 7) + kTile * kTile * (c >> 6);
+}
+
+template <typename real, bool kTape>
 struct WarpTile {
-    real kv[kTile3];       // known values of the brick and its face halo
-    alignas(16) real tv[kB3];          // current |psi| of the brick's cells
-    alignas(16) uint8_t tp[kB3];       // upwind sets (tape)
+    alignas(16) real kv[kMTile];       // brick (marked unless known) and face halo
+    alignas(16) uint8_t tp[kTape ? kB3 : 16];   // upwind sets (with a tape)
     alignas(16) uint16_t list[kB3];    // compacted cells to solve (the tags
                                        // while staging and writing back)
     unsigned improved[32]; // per owner lane: cells whose value dropped
 };
-static_assert(sizeof(WarpTile<float>) % 16 == 0 && sizeof(WarpTile<double>) % 16 == 0,
+static_assert(sizeof(WarpTile<float, false>) % 16 == 0 && sizeof(WarpTile<double, false>) % 16 == 0 &&
+                  sizeof(WarpTile<float, true>) % 16 == 0 && sizeof(WarpTile<double, true>) % 16 == 0,
               "every warp's tile starts on a 16-byte boundary");
+static_assert((kMT0 * 8) % 16 == 0 && (kTile * 8) % 16 == 0 && (kMT0 * 4) % 8 == 0 && (kTile * 4) % 8 == 0,
+              "brick rows of the tile start on 16 (double) / 8 (float) byte boundaries");
+
+// The q-th 16 bytes of a brick in brick order (cells c = x + 8 y + 64 z) to
+// and from the tile rows: two cells per 16 bytes in double (four per row),
+// four in float (two per row, stored as two 8-byte halves).  row_load clears
+// the marks: the brick in global memory holds |psi|.
+__device__ __forceinline__ void row_store(double *kv, int q, uint4 x)
+{
+    const int row = q >> 2;   // y + 8 z
+    reinterpret_cast<uint4 *>(kv + kMT0 + kTile * (row & 7) + kTile * kTile * (row >> 3))[q & 3] = x;
+}
+__device__ __forceinline__ void row_store(float *kv, int q, uint4 x)
+{
+    const int row = q >> 1;
+    uint2 *d = reinterpret_cast<uint2 *>(kv + kMT0 + kTile * (row & 7) + kTile * kTile * (row >> 3) + 4 * (q & 1));
+    d[0] = make_uint2(x.x, x.y);
+    d[1] = make_uint2(x.z, x.w);
+}
+__device__ __forceinline__ uint4 row_load(const double *kv, int q)
+{
+    const int row = q >> 2;
+    uint4 x = reinterpret_cast<const uint4 *>(kv + kMT0 + kTile * (row & 7) + kTile * kTile * (row >> 3))[q & 3];
+    x.y &= 0x7fffffffu;   // high words
+    x.w &= 0x7fffffffu;
+    return x;
+}
+__device__ __forceinline__ uint4 row_load(const float *kv, int q)
+{
+    const int row = q >> 1;
+    const uint2 *d =
+        reinterpret_cast<const uint2 *>(kv + kMT0 + kTile * (row & 7) + kTile * kTile * (row >> 3) + 4 * (q & 1));
+    const uint2 a = d[0], b = d[1];
+    return make_uint4(a.x & 0x7fffffffu, a.y & 0x7fffffffu, b.x & 0x7fffffffu, b.y & 0x7fffffffu);
+}
 
 // Cells of lane l next to a halo cell flagged in the per-face masks F[6]
 // (face bit = u + 8 v with (u, v) the two in-face coordinates).
@@ -636,7 +730,7 @@ struct MarchStats {
 // notify_v[2] the smallest flagged value of each side (+inf: none).
 template <typename real, bool kHetero, int kMode, bool kFresh, bool kTape, bool kAniso>
 __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s, const SolveParams &p,
-                                            double spd_const_term, WarpTile<real> &W, long long b,
+                                            double spd_const_term, WarpTile<real, kTape> &W, long long b,
                                             const unsigned long long *F_in, real bound0, real bound1,
                                             int lane, unsigned long long &notify_m,
                                             long long &notify_nb, real *notify_v, MarchStats &st)
@@ -648,7 +742,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
     real *bmin = (real *)s.bmin;
     const real INF = inf_v<real>();
     const int lx = lane & 7, lr = (lane >> 3) & 3;
-    const int tb = 111 + lx + kTile * lr;   // tile index of the lane's cell k = 0
+    const int tb = kMT0 + lx + kTile * lr;   // tile index of the lane's cell k = 0
     long long nbi[kFaces];
 #pragma unroll
     for (int f = 0; f < kFaces; ++f)
@@ -657,16 +751,19 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
 
     // ---- stage the brick ---------------------------------------------------
     // The brick's values, tags (and tape) are contiguous: 16-byte loads copy
-    // them into shared memory (the tags into the list buffer, unused until
-    // the rounds), then every lane reads its own cells from there.
+    // them into shared memory (the values into the rows of the tile, the tags
+    // into the list buffer, unused until the rounds), then every lane marks
+    // its own cells there.
     uint8_t *const stag = reinterpret_cast<uint8_t *>(W.list);
     {
         constexpr int kVecs = kB3 * (int)sizeof(real) / 16 / 32;   // 16-byte loads per lane
         const uint4 *gv = reinterpret_cast<const uint4 *>(T + base);
-        uint4 *sv4 = reinterpret_cast<uint4 *>(W.tv);
 #pragma unroll
-        for (int j = 0; j < kVecs; ++j)
-            sv4[lane + 32 * j] = kFresh ? __ldcg(gv + lane + 32 * j) : gv[lane + 32 * j];
+        for (int j = 0; j < kVecs; ++j) {
+            const int q = lane + 32 * j;
+            const uint4 x = kFresh ? __ldcg(gv + q) : gv[q];
+            row_store(W.kv, q, x);
+        }
         const uint4 *gt = reinterpret_cast<const uint4 *>(tag + base);
         reinterpret_cast<uint4 *>(stag)[lane] = kFresh ? __ldcg(gt + lane) : gt[lane];
         if (kTape) {
@@ -680,10 +777,12 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
 #pragma unroll 4
     for (int k = 0; k < 16; ++k) {
         const int c = lane + 32 * k;
-        const real v = W.tv[c];
+        const int ti = tb + 40 * (k & 1) + 100 * (k >> 1);
+        const real v = W.kv[ti];
         const uint8_t t = stag[c];
         const uint8_t sv = t & ST_MASK;
-        W.kv[tile_of(c)] = sv >= ST_KNOWN ? v : INF;
+        if (sv < ST_KNOWN)
+            W.kv[ti] = kmark(v);
         band |= (unsigned)(sv == ST_BAND) << k;
         known |= (unsigned)(sv >= ST_KNOWN) << k;
         fix |= (unsigned)(sv == ST_FIX) << k;
@@ -726,7 +825,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             const int hx = axis == 0 ? hedge : u + 1;
             const int hy = axis == 1 ? hedge : (axis == 0 ? u + 1 : v + 1);
             const int hz = axis == 2 ? hedge : v + 1;
-            W.kv[hx + kTile * hy + kTile * kTile * hz] = val;
+            W.kv[kMH0 + hx + kTile * hy + kTile * kTile * hz] = val;
             if (kMode == 0) {
                 // Algorithm 9: every known halo cell updates its neighbours
                 const unsigned bal = __ballot_sync(FULL, lt(val, INF));
@@ -783,8 +882,8 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             uint8_t cset = 0;
             if (i < n_items) {
                 c = W.list[i];
-                ti = tile_of(c);
-                tc = W.tv[c];
+                ti = mt_of(c);
+                tc = kval(W.kv[ti]);
                 const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
                 if constexpr (kAniso)
                     cand = solve_cell_w<real>(W.kv, ti, tc, sp, (real)p.wy, (real)p.wz, cset);
@@ -794,8 +893,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             __syncwarp();
             // each cell appears once in the list, so tc is still its value
             if (c >= 0 && lt(cand, tc)) {
-                W.tv[c] = cand;
-                W.kv[ti] = INF;
+                W.kv[ti] = kmark(cand);
                 if (kTape)
                     W.tp[c] = cset;
                 atomicOr(&W.improved[c & 31], 1u << (c >> 5));
@@ -814,7 +912,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         real l0 = r0, l1 = r1;
         for (unsigned m = imp; m; m &= m - 1u) {
             const int k = __ffs(m) - 1;
-            const real v = W.tv[lane + 32 * k];
+            const real v = kval(W.kv[tb + 40 * (k & 1) + 100 * (k >> 1)]);
             if ((neg >> k) & 1u)
                 l0 = vmin(l0, v);
             else
@@ -834,7 +932,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             // cells that were KNOWN when the march began
             for (unsigned m = known & ~settled; m; m &= m - 1u) {
                 const int k = __ffs(m) - 1;
-                if (!lt((neg >> k) & 1u ? m0 : m1, W.tv[lane + 32 * k]))
+                if (!lt((neg >> k) & 1u ? m0 : m1, W.kv[tb + 40 * (k & 1) + 100 * (k >> 1)]))
                     settled |= 1u << k;
             }
         }
@@ -854,12 +952,12 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         r1 = INF;
         for (unsigned m = band; m; m &= m - 1u) {
             const int k = __ffs(m) - 1;
-            const int c = lane + 32 * k;
-            const real v = W.tv[c];
+            const int ti = tb + 40 * (k & 1) + 100 * (k >> 1);
+            const real v = kval(W.kv[ti]);
             const bool ng = (neg >> k) & 1u;
             if (!lt(ng ? lim0 : lim1, v)) {
                 acc |= 1u << k;
-                W.kv[tb + 40 * (k & 1) + 100 * (k >> 1)] = v;
+                W.kv[ti] = v;
             } else if (ng) {
                 r0 = vmin(r0, v);
             } else {
@@ -899,7 +997,8 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
 #pragma unroll 2
     for (int k = 0; k < 16; ++k) {
         const int c = lane + 32 * k;
-        const real v = W.tv[c];
+        const int ti = tb + 40 * (k & 1) + 100 * (k >> 1);
+        const real v = kval(W.kv[ti]);
         uint8_t t;
         if ((out >> k) & 1u)
             t = TG_OUT | ST_FAR;
@@ -916,7 +1015,6 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         stag[c] = t;
         if (kMode == 1 && ((chg >> k) & 1u)) {
             const int y = lr + 4 * (k & 1), z = k >> 1;
-            const int ti = tile_of(c);
             bool flagged = false;
             if (lx == 0 && lt(v, W.kv[ti - 1])) {
                 fo0 |= 1ull << (y + 8 * z);
@@ -950,15 +1048,16 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
             }
         }
     }
-    // write back with 16-byte stores from shared memory
+    // write back with 16-byte stores from the rows of the tile (marks cleared)
     __syncwarp();
     {
         constexpr int kVecs = kB3 * (int)sizeof(real) / 16 / 32;
         uint4 *gv = reinterpret_cast<uint4 *>(T + base);
-        const uint4 *sv4 = reinterpret_cast<const uint4 *>(W.tv);
 #pragma unroll
-        for (int j = 0; j < kVecs; ++j)
-            gv[lane + 32 * j] = sv4[lane + 32 * j];
+        for (int j = 0; j < kVecs; ++j) {
+            const int q = lane + 32 * j;
+            gv[q] = row_load(W.kv, q);
+        }
         reinterpret_cast<uint4 *>(tag + base)[lane] = reinterpret_cast<const uint4 *>(stag)[lane];
         if (kTape)
             reinterpret_cast<uint4 *>(s.tape + base)[lane] = reinterpret_cast<const uint4 *>(W.tp)[lane];
@@ -1010,12 +1109,12 @@ __device__ __forceinline__ void flush_stats(Control *ctrl, MarchStats &st, int l
 // a shared counter) with the change masks the select kernel moved to the
 // inbox; changes are flagged in the neighbours' live masks and dirty flags.
 template <typename real, bool kHetero, int kMode, bool kTape, bool kAniso>
-__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real, kTape>())
     k_march(Geom g, DeviceState s, SolveParams p, double spd_const_term, int which)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    WarpTile<real, kTape> &W = reinterpret_cast<WarpTile<real, kTape> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
     if (kMode == 1 && ctrl->done)
         return;
@@ -1103,12 +1202,12 @@ __global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
 // ---------------------------------------------------------------------------
 
 template <typename real, bool kHetero, bool kTape, bool kAniso>
-__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real, kTape>())
     k_march_persistent(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    WarpTile<real, kTape> &W = reinterpret_cast<WarpTile<real, kTape> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
     if (ctrl->done)
         return;
@@ -1419,12 +1518,12 @@ __device__ void next_job(Control *c, unsigned long long *q, unsigned long long c
 }
 
 template <typename real, bool kHetero, bool kTape, bool kAniso>
-__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real>())
+__global__ void __launch_bounds__(kMarchWarps * 32, march_min_blocks<real, kTape>())
     k_march_continuous(Geom g, DeviceState s, SolveParams p, double spd_const_term)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile<real> &W = reinterpret_cast<WarpTile<real> *>(smem_raw)[warp];
+    WarpTile<real, kTape> &W = reinterpret_cast<WarpTile<real, kTape> *>(smem_raw)[warp];
     Control *ctrl = s.ctrl;
     if (ctrl->done)
         return;
@@ -1822,7 +1921,7 @@ __global__ void k_layer_integrate(Geom g, real *T, uint8_t *tag, real *bmin, int
         const long long b = ((long long)(k >> 3) * g.nby + (j >> 3)) * g.nbx + (i >> 3);
         const long long e = b * kB3 + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
         const real v = in[p];
-        const real a = v < (real)0 ? -v : v;
+        const real a = kval(v);   // |v|, -0 included
         const uint8_t tg = tag[e];
         if ((tg & ST_MASK) == ST_FIX || !(a < inf_v<real>()))
             continue;
@@ -2007,8 +2106,8 @@ int grid_for(long long n, int threads, int cap)
     return (int)b;
 }
 
-template <typename real>
-size_t march_smem() { return sizeof(WarpTile<real>) * kMarchWarps; }
+template <typename real, bool kTape>
+size_t march_smem() { return sizeof(WarpTile<real, kTape>) * kMarchWarps; }
 
 // Trace: restart, phase and list length of a march launch.
 __global__ void k_trace(const Control *c, int which, int phase, int *out)
@@ -2066,7 +2165,6 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
     const int rb = grid_for(g.nbricks, 256, 4096);
     const bool het = s.spd != nullptr, tape = s.tape != nullptr;
     const double sct = p.spd_term;
-    const size_t sm = march_smem<real>();
     k_reduce<real><<<rb, 256, 0, st>>>(g, (const real *)s.bmin, s.inmin, s.dirty, s.ctrl);
     k_control<<<1, 1, 0, st>>>(s.ctrl, p.width, p.stride, p.max_restarts);
     if (one_launch_schedule(p.schedule)) {
@@ -2077,6 +2175,7 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             cudaEventRecord(ev[0], st);
         with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
             constexpr bool h = decltype(H)::value, t = decltype(P)::value, an = decltype(A)::value;
+            const size_t sm = march_smem<real, t>();
             if (p.schedule == kScheduleContinuous)
                 k_march_continuous<real, h, t, an><<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct);
             else
@@ -2098,7 +2197,8 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
             cudaEventRecord(ev[2 * pass], st);
         with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
             k_march<real, decltype(H)::value, 1, decltype(P)::value, decltype(A)::value>
-                <<<s.march_ctas, kMarchWarps * 32, sm, st>>>(g, s, p, sct, which);
+                <<<s.march_ctas, kMarchWarps * 32, march_smem<real, decltype(P)::value>(), st>>>(g, s, p, sct,
+                                                                                                  which);
         });
         if (ev)
             cudaEventRecord(ev[2 * pass + 1], st);
@@ -2112,31 +2212,40 @@ cudaError_t front_init_impl(const Geom &g, const DeviceState &s, const SolvePara
 {
     const long long need = (g.nbricks + kMarchWarps - 1) / kMarchWarps;
     const int nb = (int)(need < s.march_ctas ? need : s.march_ctas);
-    const size_t sm = march_smem<real>();
     with_flags(s.spd != nullptr, s.tape != nullptr, p.aniso != 0, [&](auto H, auto P, auto A) {
         k_march<real, decltype(H)::value, 0, decltype(P)::value, decltype(A)::value>
-            <<<nb, kMarchWarps * 32, sm, st>>>(g, s, p, p.spd_term, 0);
+            <<<nb, kMarchWarps * 32, march_smem<real, decltype(P)::value>(), st>>>(g, s, p, p.spd_term, 0);
     });
     return cudaGetLastError();
 }
 
+// Shared-memory attributes of every march kernel; returns the resident CTAs
+// per SM of the march kernels with or without the tape (the smallest over
+// the kernels a solve may launch).
 template <typename real>
-int configure_march()
+int configure_march(bool tape)
 {
-    const int sm = (int)march_smem<real>();
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    int n = 1 << 20;
     for (int f = 0; f < 8; ++f)
         with_flags((f & 1) != 0, (f & 2) != 0, (f & 4) != 0, [&](auto H, auto P, auto A) {
             constexpr bool hh = decltype(H)::value, tt = decltype(P)::value, an = decltype(A)::value;
+            const int sm = (int)march_smem<real, tt>();
             cudaFuncSetAttribute(k_march<real, hh, 1, tt, an>, attr, sm);
             cudaFuncSetAttribute(k_march<real, hh, 0, tt, an>, attr, sm);
             cudaFuncSetAttribute(k_march_persistent<real, hh, tt, an>, attr, sm);
             cudaFuncSetAttribute(k_march_continuous<real, hh, tt, an>, attr, sm);
+            if (tt != tape)
+                return;
+            int k = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_march_continuous<real, hh, tt, an>,
+                                                          kMarchWarps * 32, sm);
+            n = k < n ? k : n;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_march<real, hh, 1, tt, an>, kMarchWarps * 32,
+                                                          sm);
+            n = k < n ? k : n;
         });
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<real, true, 1, true, false>, kMarchWarps * 32,
-                                                  sm);
-    return n > 0 ? n : 1;
+    return n > 0 && n < (1 << 20) ? n : 1;
 }
 
 }  // namespace
@@ -2261,13 +2370,15 @@ cudaError_t launch_march_to(int dtype, const Geom &g, const DeviceState &s, cons
         k_seed<double><<<rb, 256, 0, st>>>(g, (const double *)s.bmin, s.inmin, s.ctrl, s.queued, s.queue);
         with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
             k_march_persistent<double, decltype(H)::value, decltype(P)::value, decltype(A)::value>
-                <<<s.march_ctas, kMarchWarps * 32, march_smem<double>(), st>>>(g, s, p, p.spd_term);
+                <<<s.march_ctas, kMarchWarps * 32, march_smem<double, decltype(P)::value>(), st>>>(g, s, p,
+                                                                                                   p.spd_term);
         });
     } else {
         k_seed<float><<<rb, 256, 0, st>>>(g, (const float *)s.bmin, s.inmin, s.ctrl, s.queued, s.queue);
         with_flags(het, tape, p.aniso != 0, [&](auto H, auto P, auto A) {
             k_march_persistent<float, decltype(H)::value, decltype(P)::value, decltype(A)::value>
-                <<<s.march_ctas, kMarchWarps * 32, march_smem<float>(), st>>>(g, s, p, p.spd_term);
+                <<<s.march_ctas, kMarchWarps * 32, march_smem<float, decltype(P)::value>(), st>>>(g, s, p,
+                                                                                                  p.spd_term);
         });
     }
     return cudaGetLastError();
@@ -2353,9 +2464,9 @@ cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bg
     return cudaGetLastError();
 }
 
-int march_blocks_per_sm(int dtype)
+int march_blocks_per_sm(int dtype, bool tape)
 {
-    return dtype == 1 ? configure_march<double>() : configure_march<float>();
+    return dtype == 1 ? configure_march<double>(tape) : configure_march<float>(tape);
 }
 
 }  // namespace fmmgb

@@ -177,7 +177,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     s.ctrl = (Control *)(base + kOffCtrl);
     s.spd = nullptr;
     s.tape = nullptr;
-    const int per_sm = march_blocks_per_sm(cfg->dtype);
+    const int per_sm = march_blocks_per_sm(cfg->dtype, false);
     s.march_ctas = cfg->ctas > 0 ? cfg->ctas : sms * per_sm;
 
     SolveParams p;

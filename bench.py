@@ -80,10 +80,14 @@ def traffic_record(kernel, dtype, workload):
     return _profile_record("k_march_traffic.txt", kernel, dtype, workload)
 
 
-def ops_record(kernel, dtype, workload):
-    """fp64 flops (fp64 kernels) or issued warp instructions (fp32 kernels)
-    per finalised point."""
-    return _profile_record("k_march_ops.txt", kernel, dtype, workload)
+def issue_record(kernel, dtype, workload):
+    """Warp instructions issued per finalised point."""
+    return _profile_record("k_march_issue.txt", kernel, dtype, workload)
+
+
+def dpipe_record(kernel, dtype, workload):
+    """Double-pipe thread instructions (DFMA + DADD + DMUL) per finalised point."""
+    return _profile_record("k_march_dpipe.txt", kernel, dtype, workload)
 
 
 class ClockSampler:
@@ -487,30 +491,31 @@ def roofline_hbm(r, pts, alg, kernel, dt, workload, peak, peak_kind):
 
 
 def roofline_alu(r, pts, kernel, dt, workload, fp64_peak, sms, sm_mhz):
-    """Arithmetic roofline of the dominant kernel.  fp64: double-pipe thread
-    instructions (DFMA + DADD + DMUL, ncu counts per point x points) per
-    launch over the launch time, against the measured double FMA instruction
-    rate (fmm_probe_fma_rate / 2: every one of them occupies the double pipe
-    like an FMA).  fp32: issued warp instructions per launch over the launch
-    time, against the issue rate of the SMs (4 schedulers x 1 warp
-    instruction per clock x SMs x max clock)."""
+    """Instruction-issue roofline of the dominant kernel: warp instructions
+    issued per launch (ncu's count per point x points) over the launch time,
+    against the issue rate of the SMs (4 schedulers x 1 warp instruction per
+    clock x SMs x the clock sampled during the run).  For fp64 the double
+    pipe is given beside it: double-pipe thread instructions (DFMA + DADD +
+    DMUL) per second against the measured double FMA rate
+    (fmm_probe_fma_rate / 2: each of them occupies the pipe like an FMA)."""
     launches = max(r["march_launches"], 1.0)
     avg_s = r["march_ms"] / launches / 1e3
-    per_pt = ops_record(kernel, dt, workload)
-    if dt == "f64":
-        peak = fp64_peak / 2 / 1e12 if fp64_peak else None
-        ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None
-        return {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": peak,
-                "unit": "T double-pipe instructions/s",
-                "frac": (ach / peak) if (ach and peak) else None, "kernel": kernel,
-                "peak_kind": "measured (fmm_probe_fma_rate, double FMA chains, FMAs/s)",
-                "ops_per_point": per_pt}
+    per_pt = issue_record(kernel, dt, workload)
     peak = 4 * sms * sm_mhz * 1e6 / 1e12
     ach = per_pt * pts / launches / avg_s / 1e12 if (per_pt and avg_s > 0) else None
-    return {"bound": "alu", "pipe": "issue", "achieved": ach, "peak": peak, "unit": "Tinst/s",
-            "frac": (ach / peak) if ach else None, "kernel": kernel,
-            "peak_kind": f"derived: 4 warp instructions per clock per SM x {sms} SMs x {sm_mhz:.0f} MHz",
-            "ops_per_point": per_pt}
+    out = {"bound": "alu", "pipe": "issue", "achieved": ach, "peak": peak, "unit": "Tinst/s",
+           "frac": (ach / peak) if ach else None, "kernel": kernel,
+           "peak_kind": f"derived: 4 warp instructions per clock per SM x {sms} SMs x {sm_mhz:.0f} MHz",
+           "ops_per_point": per_pt}
+    if dt == "f64":
+        dp = dpipe_record(kernel, dt, workload)
+        dpeak = fp64_peak / 2 / 1e12 if fp64_peak else None
+        dach = dp * pts / launches / avg_s / 1e12 if (dp and avg_s > 0) else None
+        out["fp64_pipe"] = {"achieved": dach, "peak": dpeak, "unit": "T double-pipe instructions/s",
+                            "frac": (dach / dpeak) if (dach and dpeak) else None,
+                            "peak_kind": "measured (fmm_probe_fma_rate, double FMA chains, FMAs/s)",
+                            "ops_per_point": dp}
+    return out
 
 
 def kernel_name(params):

@@ -1330,6 +1330,25 @@ __device__ __forceinline__ void queue_push_warp(Control *c, unsigned long long *
 // last took its masks, +inf when none is recorded.
 constexpr unsigned long long kInminNone = ~0ull;
 template <typename real>
+__device__ __forceinline__ real inmin_bits(unsigned long long v)
+{
+    return v >= 0x7ff0000000000000ull ? inf_v<real>() : (real)__longlong_as_double((long long)v);
+}
+// both BAND minima of a brick (adjacent, 16- or 8-byte aligned) in one load
+__device__ __forceinline__ void ld_pair(const double *p, double &a, double &b)
+{
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const float *p, float &a, float &b)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+
+template <typename real>
 __device__ __forceinline__ real inmin_value(const unsigned long long *inmin, long long j)
 {
     const unsigned long long v = vloadu(inmin + j);
@@ -1347,17 +1366,35 @@ __device__ __forceinline__ void scan_chunk(const Geom &g, const DeviceState &s, 
     const unsigned long long cap = (unsigned long long)g.nbricks;
     real l0 = INF, l1 = INF;
     const long long first = (long long)ch * kScanChunk;
-    for (int j = 0; j < kScanChunk / 32; ++j) {
-        const long long b = first + 32 * j + lane;
-        bool sel = false;
-        if (b < g.nbricks) {
-            const real m0 = vmin(__ldcg(bmin + 2 * b), inmin_value<real>(s.inmin, 2 * b));
-            const real m1 = vmin(__ldcg(bmin + 2 * b + 1), inmin_value<real>(s.inmin, 2 * b + 1));
+    // kScanBatch bricks per lane at a time: both minima of a brick in one
+    // load, both flagged values in another, all loads of a batch in flight
+    // together (the scan is a chain of L2 round trips otherwise)
+    constexpr int kScanBatch = 2;
+    static_assert((kScanChunk / 32) % kScanBatch == 0, "whole batches per chunk");
+    for (int j0 = 0; j0 < kScanChunk / 32; j0 += kScanBatch) {
+        real bm[kScanBatch][2];
+        ulonglong2 im[kScanBatch];
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) {
+            const long long b = first + 32 * (j0 + u) + lane;
+            if (b < g.nbricks) {
+                ld_pair(bmin + 2 * b, bm[u][0], bm[u][1]);
+                im[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(s.inmin + 2 * b));
+            } else {
+                bm[u][0] = bm[u][1] = INF;
+                im[u] = make_ulonglong2(kInminNone, kInminNone);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) {
+            const long long b = first + 32 * (j0 + u) + lane;
+            const real m0 = vmin(bm[u][0], inmin_bits<real>(im[u].x));
+            const real m1 = vmin(bm[u][1], inmin_bits<real>(im[u].y));
             l0 = vmin(l0, m0);
             l1 = vmin(l1, m1);
-            sel = (lt(m0, INF) && !lt(bd0, m0)) || (lt(m1, INF) && !lt(bd1, m1));
+            const bool sel = b < g.nbricks && ((lt(m0, INF) && !lt(bd0, m0)) || (lt(m1, INF) && !lt(bd1, m1)));
+            queue_push_warp(c, s.queue, cap, s.queued, b, sel, lane);
         }
-        queue_push_warp(c, s.queue, cap, s.queued, b, sel, lane);
     }
     l0 = warp_min(l0);
     l1 = warp_min(l1);

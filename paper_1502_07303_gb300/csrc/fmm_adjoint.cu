@@ -148,7 +148,7 @@ struct AdjTile {
     real T[kTile3];      // |psi| of the brick and its face halo
     real mu[kTile3];     // published mu (NaN = not done) of brick and halo
     uint8_t tp[kTile3];  // tape of brick and halo
-    uint8_t tg[kB3];     // tags of the brick
+    uint16_t list[kB3];  // the cells found ready in a round, compacted
 };
 
 // Tape code of axis a of cell tp: 0 none, 1 minus neighbour, 2 plus.
@@ -214,7 +214,6 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
             W.mu[ti] = m;
             // cells that were not accepted have no upwind set
             W.tp[ti] = accepted(tg) ? s.tape[base + c] : (uint8_t)0;
-            W.tg[c] = tg;
             todo |= (unsigned)(accepted(tg) && is_nan_bits(m)) << k;
         }
         // ---- halo: the face layers of the six neighbours ------------------
@@ -254,50 +253,60 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
         // The first round tests every cell still to do; later rounds only the
         // neighbours of the cells done in the round before (a cell becomes
         // ready when its last downwind neighbour is done; halo values are
-        // fixed for the pass).
+        // fixed for the pass).  Every candidate is tested before any cell of
+        // the round publishes, then the ready cells are compacted and
+        // computed 32 at a time.  Two cells ready in one round never depend
+        // on each other (a cell is ready only after all cells downwind of
+        // it), so their order does not matter.
         unsigned face_done = 0;   // bit f: a done cell has an upwind cell across face f
         unsigned done_any = 0;
         unsigned cand = todo;
+        const real wax[3] = {(real)1, (real)wy, (real)wz};
         for (;;) {
-            const int steps = (int)__reduce_max_sync(FULL, (unsigned)__popc(cand));
-            if (steps == 0)
-                break;
-            unsigned rest = cand, done_now = 0;
-            for (int j = 0; j < steps; ++j) {
-                int k = -1;
-                if (rest) {
-                    k = __ffs(rest) - 1;
-                    rest &= rest - 1u;
-                }
-                bool ready = false;
-                int ti = 0;
-                if (k >= 0) {
-                    // ready when every downwind neighbour has published: on
-                    // axis a, q = p - e_a (its upwind code 2 points at p)
-                    // and q = p + e_a (code 1)
-                    ti = tb_of(lx, lr, k);
-                    ready = true;
+            unsigned ready_mask = 0;
+            for (unsigned rest = cand; rest; rest &= rest - 1u) {
+                const int k = __ffs(rest) - 1;
+                // ready when every downwind neighbour has published: on
+                // axis a, q = p - e_a (its upwind code 2 points at p) and
+                // q = p + e_a (code 1)
+                const int ti = tb_of(lx, lr, k);
+                bool ready = true;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const int qm = ti - off[a], qp = ti + off[a];
-                        if (tape_axis(W.tp[qm], a) == 2 && is_nan_bits(W.mu[qm]))
-                            ready = false;
-                        if (tape_axis(W.tp[qp], a) == 1 && is_nan_bits(W.mu[qp]))
-                            ready = false;
-                    }
+                for (int a = 0; a < 3; ++a) {
+                    const int qm = ti - off[a], qp = ti + off[a];
+                    if (tape_axis(W.tp[qm], a) == 2 && is_nan_bits(W.mu[qm]))
+                        ready = false;
+                    if (tape_axis(W.tp[qp], a) == 1 && is_nan_bits(W.mu[qp]))
+                        ready = false;
                 }
-                // the cells of this step test before any of them publishes
-                // (a published mu is final, so the sums below may read
-                // neighbours that other lanes publish in this step)
-                __syncwarp();
-                if (ready) {
-                    // the sums only for cells that are ready (the arithmetic
-                    // of the cells still waiting would be thrown away)
+                ready_mask |= (unsigned)ready << k;
+            }
+            // compact the ready cells (warp prefix sum of the lane counts)
+            const int cnt = __popc(ready_mask);
+            int pre = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, pre, o);
+                if (lane >= o)
+                    pre += t;
+            }
+            const int n_ready = __shfl_sync(FULL, pre, 31);
+            ++rounds_total;
+            if (n_ready == 0)
+                break;
+            pre -= cnt;
+            for (unsigned m = ready_mask; m; m &= m - 1u)
+                W.list[pre++] = (uint16_t)(lane + 32 * (__ffs(m) - 1));
+            __syncwarp();
+            for (int i0 = 0; i0 < n_ready; i0 += 32) {
+                const int i = i0 + lane;
+                if (i < n_ready) {
+                    const int c = W.list[i];
+                    const int ti = tile_of(c);
                     real lam = (real)0, dsum = (real)0;
                     const real Tp = W.T[ti];
                     // unequal cells: the terms of axis a carry
                     // w_a = (h / h_a)^2 (Eq. (2) with h_i per axis)
-                    const real wax[3] = {(real)1, (real)wy, (real)wz};
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int qm = ti - off[a], qp = ti + off[a];
@@ -322,16 +331,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                                 dsum += Tp - W.T[code == 1 ? qm : qp];
                         }
                     }
-                    const int c = lane + 32 * k;
-                    const int cx = lx, cy = lr + 4 * (k & 1), cz = k >> 1;
-                    const int i = bx * kB + cx, jj = by * kB + cy, kk = bz * kB + cz;
-                    const long long nat = ((long long)kk * g.ny + jj) * g.nx + i;
+                    const int cx = c & 7, cy = (c >> 3) & 7, cz = c >> 6;
+                    const int gi = bx * kB + cx, gj = by * kB + cy, gk = bz * kB + cz;
+                    const long long nat = ((long long)gk * g.ny + gj) * g.nx + gi;
                     lam += dLdT[nat];
                     const real m = positive(dsum) ? adj_div(lam, dsum) : (real)0;
-                    W.mu[ti] = m;
                     // s_p h^2 = sqrt(q) h with q = (h/F)^2
                     const real sh2 = kHetero ? adj_sqrt(spd[base + c]) * (real)h : sh2_const;
                     dlds[nat] = m * sh2;
+                    W.mu[ti] = m;
                     const uint8_t tpc = W.tp[ti];
                     if (cx == 0 && tape_axis(tpc, 0) == 1) face_done |= 1u;
                     if (cx == 7 && tape_axis(tpc, 0) == 2) face_done |= 2u;
@@ -339,16 +347,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
                     if (cy == 7 && tape_axis(tpc, 1) == 2) face_done |= 8u;
                     if (cz == 0 && tape_axis(tpc, 2) == 1) face_done |= 16u;
                     if (cz == 7 && tape_axis(tpc, 2) == 2) face_done |= 32u;
-                    done_now |= 1u << k;
                 }
-                __syncwarp();
             }
-            todo &= ~done_now;
-            done_any |= done_now;
-            ++rounds_total;
-            if (!__any_sync(FULL, done_now != 0u))
-                break;
-            cand = neighbour_mask(done_now, lane) & todo;
+            __syncwarp();
+            todo &= ~ready_mask;
+            done_any |= ready_mask;
+            cand = neighbour_mask(ready_mask, lane) & todo;
         }
         // ---- publish mu, wake the bricks that hold upwind neighbours ------
         for (unsigned mm = done_any; mm; mm &= mm - 1u) {

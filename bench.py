@@ -612,6 +612,14 @@ def run_gpu(args):
                                   "accepted_per_point": r["stats"]["accepted"] / c2.n_points,
                                   "solves_per_point": r["stats"]["cell_solves"] / c2.n_points,
                                   "marches_per_brick": r["stats"]["brick_marches"] / r["stats"]["n_bricks"]}
+            # the bit-reproducible mode (phased schedule, pass-synchronous
+            # halos), library defaults otherwise: what reproducibility costs
+            rd = measure(fmm, torch, c2, DTS[name], args.steps, args.warmup, flush, stream,
+                         {"deterministic": True}, phi=phi)
+            others["c2"][name]["deterministic"] = {
+                "gpts": c2.n_points / rd["ms"] / 1e6, "ms": rd["ms"], "time_vs_default": rd["ms"] / r["ms"],
+                "restarts": rd["stats"]["restarts"], "marches_per_brick":
+                    rd["stats"]["brick_marches"] / rd["stats"]["n_bricks"]}
         del c2, phi
         c1 = wl.point_source(64)
         prm, _ = tune_params(autotune, torch, c1, torch.float64, stream, "sources")

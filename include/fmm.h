@@ -124,6 +124,18 @@ typedef struct {
                               is changed halo data waits until the bound
                               reaches the smallest changed value; 0 -> +inf.
                               The result does not depend on it.             */
+    int32_t deterministic; /* 1: bit-reproducible results: the phased schedule
+                              (schedule must be 0 or 1) with every brick
+                              reading its neighbours' boundary values as they
+                              stood at the end of the previous march pass, so
+                              the result depends on no timing, CTA count or
+                              launch order (the paper's synchronous exchange
+                              per restart, Sec. 4.3); about twice the time of
+                              the default, and one more array of 6 x 64
+                              values per brick; stride 0 -> 8 for FMM_F32, 4
+                              for FMM_F64 in this mode.  Single grids only (not batches, the
+                              fmm_dd_* entry points or the entry point
+                              without allocation).  0 normally.             */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */

@@ -86,8 +86,8 @@ fmm_status cuda_fail(fmm_handle *hd, cudaError_t e, const char *where)
 void free_state(fmm_handle *hd)
 {
     DeviceState &s = hd->st;
-    void *ptrs[] = {s.T, s.tag, s.spd, s.bdelta, s.tape, s.bmin, s.fresh, s.inmin, s.inbox, s.dirty,
-                    s.list[0], s.list[1], s.ctrl, hd->d_src, s.queue, s.queued};
+    void *ptrs[] = {s.T,      s.tag,      s.spd,   s.bdelta,  s.tape,   s.bmin,   s.fresh, s.inmin, s.inbox,
+                    s.dirty,  s.list[0],  s.list[1], s.ctrl,  hd->d_src, s.queue, s.queued, s.faces};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -502,6 +502,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
     if (cfg->schedule < 0 || cfg->schedule > 3)
         return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1, 2 or 3");
+    if (cfg->deterministic != 0 && cfg->schedule != 0 && cfg->schedule != kSchedulePhased)
+        return fail(nullptr, FMM_ERR_INVALID, "deterministic needs the phased schedule (schedule 0 or 1)");
     if (n_src < 0 || (n_src > 0 && !src_ijk))
         return fail(nullptr, FMM_ERR_INVALID, "bad source list");
     if (speed && !aligned16(speed))
@@ -530,13 +532,15 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     SolveParams &p = hd->params;
     set_spacing(p, cfg->h, cfg->hy, cfg->hz);
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
-    const double stride_h = cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype);
+    const double stride_h = cfg->stride > 0.0       ? cfg->stride
+                            : cfg->deterministic ? default_stride_deterministic(cfg->dtype)
+                                                 : default_stride(cfg->dtype);
     p.stride = stride_h * cfg->h;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
-    p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
-                 : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
-                                                        : kScheduleContinuous;
+    p.schedule = cfg->schedule == kSchedulePhased || cfg->deterministic ? kSchedulePhased
+                 : cfg->schedule == kSchedulePersistent                 ? kSchedulePersistent
+                                                                        : kScheduleContinuous;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();
@@ -579,6 +583,8 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
     ALLOC(s.ctrl, sizeof(Control));
     if (cfg->record_tape)
         ALLOC(s.tape, cells);
+    if (cfg->deterministic)
+        ALLOC(s.faces, nb * kFaces * 64 * hd->rsize);
     if (n_src > 0) {
         ALLOC(hd->d_src, (size_t)n_src * 3 * sizeof(long long));
         e = cudaMemcpy(hd->d_src, src_ijk, (size_t)n_src * 3 * sizeof(long long), cudaMemcpyHostToDevice);
@@ -738,6 +744,8 @@ fmm_status fmm_resume(fmm_handle *hd, int64_t more_restarts, void *T_out, uint8_
     hd->pre_launches = 0;
     cudaError_t e = cudaMemcpyAsync(hd->st.ctrl, hd->h_ctrl, sizeof(Control), cudaMemcpyHostToDevice,
                                     hd->stream);
+    if (e == cudaSuccess && hd->st.faces)
+        e = launch_faces_build(hd->cfg.dtype, hd->geom, hd->st, hd->stream);   // from the stopped state
     if (e != cudaSuccess) {
         hd->params.max_restarts = keep;
         return cuda_fail(hd, e, "fmm_resume: control block");
@@ -778,6 +786,8 @@ fmm_status fmm_dd_start(fmm_handle *hd, const void *phi0, int64_t extra_lo, int6
         return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
     if (hd->n_grids)
         return fail(hd, FMM_ERR_STATE, "batch handles have no domain decomposition");
+    if (hd->st.faces)
+        return fail(hd, FMM_ERR_STATE, "the fmm_dd_* entry points have no deterministic mode");
     if (phi0 && (!aligned16(phi0) || is_host(phi0)))
         return fail(hd, FMM_ERR_INVALID, "phi0 must be 16-byte aligned device memory");
     if (extra_lo < 0 || extra_lo > 1 || extra_hi < 0 || extra_hi > 1)
@@ -996,6 +1006,8 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
         return fail(nullptr, FMM_ERR_INVALID, "bad width, stride, bucket, ahead or exchange_passes");
     if (cfg->record_tape)
         return fail(nullptr, FMM_ERR_INVALID, "batches keep no tape (record_tape must be 0)");
+    if (cfg->deterministic)
+        return fail(nullptr, FMM_ERR_INVALID, "batches have no deterministic mode (deterministic must be 0)");
     if (cfg->hy != 0.0 || cfg->hz != 0.0)
         return fail(nullptr, FMM_ERR_INVALID, "batches use cubic cells (hy and hz must be 0)");
     std::vector<BatchGrid> grids((size_t)n_grids);

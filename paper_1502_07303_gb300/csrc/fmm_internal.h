@@ -154,6 +154,10 @@ inline bool one_launch_schedule(int schedule)
 // Defaults of the restart parameters (units of h and of the bucket width),
 // measured on GB300 for 8^3 bricks.
 inline double default_stride(int dtype) { return dtype == 1 ? 1.0 : 2.0; }
+// deterministic mode (phased schedule, pass-synchronous halos): information
+// crosses one brick per pass, so wider strides pay (1024^3 sphere: fp64
+// 722 / 493 / 529 ms at 1 / 4 / 8 h, fp32 374 / 278 / 238 ms at 2 / 4 / 8 h)
+inline double default_stride_deterministic(int dtype) { return dtype == 1 ? 4.0 : 8.0; }
 inline int default_passes(int dtype) { return dtype == 1 ? 1 : 2; }
 // continuous schedule: look-ahead of a brick march beyond the bound (units of
 // h; +inf: a brick marches to its end once the bound reaches its smallest
@@ -176,6 +180,8 @@ struct DeviceState {
                                  // neighbour flagged in the masks since the
                                  // brick last took them (bits of a double;
                                  // all ones: none recorded)
+    void *faces;        // deterministic mode, 6 x 64 per brick: its boundary
+                        // layers (known value or +inf) as of the last pass
     unsigned long long *inbox;   // 6 per brick: masks taken by the last selection
     unsigned int *dirty;         // 1 per brick: has pending overlap changes
     int *list[2];       // work lists
@@ -238,6 +244,8 @@ cudaError_t launch_reset_control(const DeviceState &s, cudaStream_t stream,
 cudaError_t launch_output(int dtype, const Geom &g, const DeviceState &s,
                           void *T_out, uint8_t *tags_out, cudaStream_t stream);
 int march_blocks_per_sm(int dtype, bool tape);
+// Deterministic mode: rebuild the boundary layers of every brick from the state.
+cudaError_t launch_faces_build(int dtype, const Geom &g, const DeviceState &s, cudaStream_t st);
 cudaError_t launch_batch_init(int dtype, const BatchGrid *grids, const int *bgrid,
                               long long nbricks, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_batch_speed(int dtype, const BatchGrid *grids, const int *bgrid,

@@ -810,7 +810,10 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
         for (int half = 0; half < 2; ++half) {
             const int q = lane + 32 * half, u = q & 7, v = q >> 3;
             real val = INF;
-            if (nb >= 0) {
+            if (kMode == 1 && nb >= 0 && s.faces) {
+                // deterministic mode: the neighbour's layer as of the last pass
+                val = __ldcg((const real *)s.faces + nb * (kFaces * 64) + (f ^ 1) * 64 + q);
+            } else if (nb >= 0) {
                 const int edge = dir < 0 ? kB - 1 : 0;
                 const int cx = axis == 0 ? edge : u;
                 const int cy = axis == 1 ? edge : (axis == 0 ? u : v);
@@ -2146,6 +2149,43 @@ int grid_for(long long n, int threads, int cap)
 template <typename real, bool kTape>
 size_t march_smem() { return sizeof(WarpTile<real, kTape>) * kMarchWarps; }
 
+// Deterministic mode: face f of brick b is its boundary layer on side f
+// (0..5 = -x, +x, -y, +y, -z, +z), cell q = u + 8 v in the in-face
+// coordinates of the halo loader of march_brick, holding the known value or
+// +inf.  A march pass reads its neighbours' faces and the faces of the bricks
+// it marched are rebuilt after the pass (which >= 0: work list `which`), so
+// a pass sees the state of the previous one whatever the order of its
+// marches.  which < 0: every brick.
+template <typename real>
+__global__ void k_faces_build(Geom g, const real *__restrict__ T, const uint8_t *__restrict__ tag,
+                              const Control *ctrl, const int *list, int which, real *faces)
+{
+    const long long nb = which < 0 ? g.nbricks : (long long)ctrl->n_list[which];
+    const long long n = nb * (kFaces * 64);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long bi = e / (kFaces * 64);
+        const int r = (int)(e - bi * (kFaces * 64));
+        const long long b = which < 0 ? bi : (long long)list[bi];
+        const int f = r >> 6, q = r & 63, u = q & 7, v = q >> 3;
+        const int axis = f >> 1;
+        const int edge = (f & 1) ? kB - 1 : 0;
+        const int cx = axis == 0 ? edge : u;
+        const int cy = axis == 1 ? edge : (axis == 0 ? u : v);
+        const int cz = axis == 2 ? edge : v;
+        const long long ci = b * kB3 + cx + kB * cy + kB * kB * cz;
+        faces[b * (kFaces * 64) + r] = is_known(tag[ci]) ? T[ci] : inf_v<real>();
+    }
+}
+
+template <typename real>
+void faces_build(const Geom &g, const DeviceState &s, int which, cudaStream_t st)
+{
+    const int nb = grid_for(g.nbricks * (kFaces * 64), 256, 152 * 32);
+    k_faces_build<real><<<nb, 256, 0, st>>>(g, (const real *)s.T, s.tag, s.ctrl,
+                                            which < 0 ? nullptr : s.list[which], which, (real *)s.faces);
+}
+
 // Trace: restart, phase and list length of a march launch.
 __global__ void k_trace(const Control *c, int which, int phase, int *out)
 {
@@ -2237,6 +2277,8 @@ cudaError_t restart_impl(const Geom &g, const DeviceState &s, const SolveParams 
                 <<<s.march_ctas, kMarchWarps * 32, march_smem<real, decltype(P)::value>(), st>>>(g, s, p, sct,
                                                                                                   which);
         });
+        if (s.faces)
+            faces_build<real>(g, s, which, st);
         if (ev)
             cudaEventRecord(ev[2 * pass + 1], st);
     }
@@ -2253,6 +2295,8 @@ cudaError_t front_init_impl(const Geom &g, const DeviceState &s, const SolvePara
         k_march<real, decltype(H)::value, 0, decltype(P)::value, decltype(A)::value>
             <<<nb, kMarchWarps * 32, march_smem<real, decltype(P)::value>(), st>>>(g, s, p, p.spd_term, 0);
     });
+    if (s.faces)
+        faces_build<real>(g, s, -1, st);
     return cudaGetLastError();
 }
 
@@ -2498,6 +2542,15 @@ cudaError_t launch_batch_output(int dtype, const BatchGrid *grids, const int *bg
         k_batch_output<double><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (const double *)s.T, s.tag);
     else
         k_batch_output<float><<<nb, 256, 0, st>>>(grids, bgrid, nbricks, (const float *)s.T, s.tag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_faces_build(int dtype, const Geom &g, const DeviceState &s, cudaStream_t st)
+{
+    if (dtype == 1)
+        faces_build<double>(g, s, -1, st);
+    else
+        faces_build<float>(g, s, -1, st);
     return cudaGetLastError();
 }
 

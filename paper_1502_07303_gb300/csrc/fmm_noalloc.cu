@@ -133,6 +133,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
         return error(FMM_ERR_INVALID, "schedule must be 0, 1, 2 or 3");
     if (cfg->record_tape)
         return error(FMM_ERR_INVALID, "the no-allocation entry point keeps no tape (record_tape must be 0)");
+    if (cfg->deterministic)
+        return error(FMM_ERR_INVALID, "the no-allocation entry point has no deterministic mode");
     if (!phi0 || ((uintptr_t)phi0 & 15u) || !T_out || ((uintptr_t)T_out & 15u))
         return error(FMM_ERR_INVALID, "phi0 and T_out must be 16-byte aligned device pointers");
     Geom g;

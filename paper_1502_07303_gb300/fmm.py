@@ -39,7 +39,8 @@ class FmmConfig(ctypes.Structure):
                 ("time_kernels", ctypes.c_int32), ("exchange_passes", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32),
-                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("ahead", ctypes.c_double)]
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("ahead", ctypes.c_double),
+                ("deterministic", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
@@ -170,12 +171,16 @@ class Solver:
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
                  max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
                  schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, ahead=0.0, stream=None,
-                 tuned=True):
+                 tuned=True, deterministic=False):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.code, self.dtype = _dtype_code(dtype)
         self.stream = stream
+        if deterministic:
+            # the phased schedule with pass-synchronous halos; the tuned
+            # schedules do not apply
+            tuned = False
         if tuned:
             # parameters left at 0 take the autotuner's cached values (if any)
             kind = "reinit" if sources is None else (
@@ -206,6 +211,7 @@ class Solver:
         cfg.wait_limit_ms = int(wait_limit_ms)
         cfg.hold_queue = int(hold_queue)
         cfg.ahead = float(ahead)
+        cfg.deterministic = 1 if deterministic else 0
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)

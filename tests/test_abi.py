@@ -130,3 +130,21 @@ def test_header_compiles_as_c_and_links(tmp_path):
     cfg_size, stats_size = (int(v) for v in r.stdout.split())
     assert cfg_size == ctypes.sizeof(fmm.FmmConfig)
     assert stats_size == ctypes.sizeof(fmm.FmmStats)
+
+
+def test_deterministic_mode_needs_the_phased_schedule():
+    """fmm_create refuses deterministic = 1 with the persistent or continuous
+    schedule (argument checks run before any CUDA call: no GPU needed)."""
+    from paper_1502_07303_gb300 import fmm
+    lib = fmm.load()
+    for sched in (2, 3):
+        cfg = fmm.FmmConfig()
+        cfg.nx = cfg.ny = cfg.nz = 8
+        cfg.h = 0.125
+        cfg.dtype = 0
+        cfg.schedule = sched
+        cfg.deterministic = 1
+        h = ctypes.c_void_p()
+        rc = lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h))
+        assert rc == fmm.FMM_ERR_INVALID and not h.value
+        assert b"deterministic" in lib.fmm_last_error(None)

@@ -440,28 +440,21 @@ __device__ __forceinline__ bool nonneg(float v)
 // axis's cell size).  The level set may extend zlo layers below z = 0 and zhi
 // layers above z = nz - 1 (phi points at layer 0): a subdomain of a
 // decomposed grid sees the layers beyond its ghost layers, so its interface
-// cells are those of the whole grid.
+// cells are those of the whole grid.  reinit_load reads the cell and its six
+// neighbours (a neighbour outside the grid reads the cell itself, which never
+// changes sign), reinit_eval computes psi and the tag from them; a kernel
+// issues the loads of all its cells before the first evaluation.
 template <typename real>
-__device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx, int ny, int nz,
-                                            int i, int j, int k, double hx, double hy, double hz,
-                                            real &Tv, uint8_t &tg, int zlo = 0, int zhi = 0)
+__device__ __forceinline__ void reinit_load(const real *__restrict__ phi, int nx, int ny, int nz, int i,
+                                            int j, int k, int zlo, int zhi, real &fc, real fn[6])
 {
-    const double hs[3] = {hx, hy, hz};
     const long long sx = 1, sy = nx, sz = (long long)nx * ny;
     const long long p = (long long)k * sz + (long long)j * sy + i;
-    const real fc = phi[p];
-    // sign tests on the bit patterns (phi >= 0: sign bit clear, or -0): the
-    // FP64 pipe's comparisons would bound the whole pass for double grids
-    const bool pos = nonneg(fc);
-    real d[3];
-    bool any = false;
+    fc = phi[p];
     const int co[3] = {i, j, k};
     const int lo[3] = {0, 0, -zlo};
     const int ext[3] = {nx, ny, nz + zhi};
     const long long st[3] = {sx, sy, sz};
-    // the six neighbours first, all loads in flight together (a neighbour
-    // outside the grid reads the cell itself, which never changes sign)
-    real fn[6];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -471,6 +464,18 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
             const long long off = (q < lo[a] || q >= ext[a]) ? 0ll : (dir < 0 ? -st[a] : st[a]);
             fn[2 * a + s] = phi[p + off];
         }
+}
+
+template <typename real>
+__device__ __forceinline__ void reinit_eval(real fc, const real fn[6], double hx, double hy, double hz,
+                                            real &Tv, uint8_t &tg)
+{
+    const double hs[3] = {hx, hy, hz};
+    // sign tests on the bit patterns (phi >= 0: sign bit clear, or -0): the
+    // FP64 pipe's comparisons would bound the whole pass for double grids
+    const bool pos = nonneg(fc);
+    real d[3];
+    bool any = false;
     bool cross[6];
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
@@ -510,27 +515,45 @@ __device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx
 }
 
 template <typename real>
+__device__ __forceinline__ void reinit_cell(const real *__restrict__ phi, int nx, int ny, int nz,
+                                            int i, int j, int k, double hx, double hy, double hz,
+                                            real &Tv, uint8_t &tg, int zlo = 0, int zhi = 0)
+{
+    real fc, fn[6];
+    reinit_load<real>(phi, nx, ny, nz, i, j, k, zlo, zhi, fc, fn);
+    reinit_eval<real>(fc, fn, hx, hy, hz, Tv, tg);
+}
+
+template <typename real>
 __global__ void __launch_bounds__(kInitThreads) k_init_reinit(Geom g, double hx, double hy, double hz,
                                                               const real *__restrict__ phi, real *T,
                                                               uint8_t *tag, int zlo, int zhi)
 {
+    static_assert(kB3 == 2 * kInitThreads, "two cells per thread");
     for (int b = blockIdx.x; b < (int)g.nbricks; b += gridDim.x) {
         int bx, by, bz;
         brick_xyz32(g, b, bx, by, bz);
         const long long base = (long long)b * kB3;
-        for (int c = threadIdx.x; c < kB3; c += kInitThreads) {
-            const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
-            if (i >= g.nx || j >= g.ny || k >= g.nz) {
-                T[base + c] = inf_v<real>();
-                tag[base + c] = TG_OUT | ST_FAR;
-                continue;
-            }
-            real Tv;
-            uint8_t tg;
-            reinit_cell<real>(phi, g.nx, g.ny, g.nz, i, j, k, hx, hy, hz, Tv, tg, zlo, zhi);
-            T[base + c] = Tv;
-            tag[base + c] = tg;
-        }
+        // cells c and c + 256 of the brick: z and z + 4
+        const int c = threadIdx.x;
+        const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
+        const bool in0 = i < g.nx && j < g.ny && k < g.nz;
+        const bool in1 = i < g.nx && j < g.ny && k + 4 < g.nz;
+        real fc0 = (real)0, fc1 = (real)0, fn0[6], fn1[6];
+        if (in0)
+            reinit_load<real>(phi, g.nx, g.ny, g.nz, i, j, k, zlo, zhi, fc0, fn0);
+        if (in1)
+            reinit_load<real>(phi, g.nx, g.ny, g.nz, i, j, k + 4, zlo, zhi, fc1, fn1);
+        real Tv0 = inf_v<real>(), Tv1 = inf_v<real>();
+        uint8_t tg0 = TG_OUT | ST_FAR, tg1 = TG_OUT | ST_FAR;
+        if (in0)
+            reinit_eval<real>(fc0, fn0, hx, hy, hz, Tv0, tg0);
+        if (in1)
+            reinit_eval<real>(fc1, fn1, hx, hy, hz, Tv1, tg1);
+        T[base + c] = Tv0;
+        tag[base + c] = tg0;
+        T[base + c + kInitThreads] = Tv1;
+        tag[base + c + kInitThreads] = tg1;
     }
 }
 
@@ -1888,24 +1911,29 @@ __global__ void __launch_bounds__(kInitThreads) k_output(Geom g, const real *__r
                                                          const uint8_t *__restrict__ tag, real *T_out,
                                                          uint8_t *tags_out)
 {
+    static_assert(kB3 == 2 * kInitThreads, "two cells per thread");
     for (int b = blockIdx.x; b < (int)g.nbricks; b += gridDim.x) {
         int bx, by, bz;
         brick_xyz32(g, b, bx, by, bz);
         const long long base = (long long)b * kB3;
-        for (int c = threadIdx.x; c < kB3; c += kInitThreads) {
-            const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
-            if (i >= g.nx || j >= g.ny || k >= g.nz)
+        // cells c and c + 256 of the brick (z and z + 4), both loaded first
+        const int c = threadIdx.x;
+        const real v0 = T[base + c], v1 = T[base + c + kInitThreads];
+        const uint8_t t0 = tag[base + c], t1 = tag[base + c + kInitThreads];
+        const int i = bx * kB + (c & 7), j = by * kB + ((c >> 3) & 7), k = bz * kB + (c >> 6);
+        if (i >= g.nx || j >= g.ny)
+            continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kk = k + 4 * h;
+            if (kk >= g.nz)
                 continue;
-            const long long p = ((long long)k * g.ny + j) * g.nx + i;
-            const long long e = base + c;
-            const real v = T[e];
-            const uint8_t tg = tag[e];
+            const real v = h ? v1 : v0;
+            const uint8_t tg = h ? t1 : t0;
             const uint8_t st = tg & ST_MASK;
-            real out = v;
-            if (st == ST_FAR)
-                out = inf_v<real>();
-            else if (tg & TG_NEG)
-                out = -v;
+            // the sign as a bit (a double negation would take the FP64 pipe)
+            const real out = st == ST_FAR ? inf_v<real>() : ((tg & TG_NEG) ? kmark(v) : v);
+            const long long p = ((long long)kk * g.ny + j) * g.nx + i;
             T_out[p] = out;
             if (tags_out)
                 tags_out[p] = st;

@@ -433,6 +433,22 @@ fmm_status fmm_selftest_fp64(const double *a, const double *b, double *sqrt_out,
                              int64_t n, void *stream);
 
 /*
+ * fmm_selftest_root -- diagnostics of the double-grid root of Algorithm 11
+ * (Sec. 2, Eq. (2) on the upwind set, solved in double-float arithmetic as
+ * the fp64 march does): for i < n, sorted upwind values m[i] <= v1[i] <=
+ * v2[i] of which the nd[i] (1..3) smallest take part, speed term q[i] =
+ * (h/F)^2 in [1e-30, 1e30]; k_out[i] = the size of the causal set the
+ * routine chose (dropping the largest value while the root does not exceed
+ * it; 0: none) and t_out[i] = its root (+inf when k = 0).  All arrays device,
+ * caller-owned, n elements; enqueued on stream (cudaStream_t), asynchronous.
+ * FMM_ERR_INVALID for n < 0 or a NULL array, FMM_ERR_CUDA if the launch
+ * fails.  (Not part of the paper: it lets a test check the causal set and
+ * the root against exact arithmetic.)
+ */
+fmm_status fmm_selftest_root(const double *m, const double *v1, const double *v2, const int32_t *nd,
+                             const double *q, double *t_out, int32_t *k_out, int64_t n, void *stream);
+
+/*
  * fmm_probe_fma_rate -- diagnostics: the device's fused multiply-add
  * throughput in float (dtype FMM_F32) or double (FMM_F64), the arithmetic
  * ceiling the march kernels are held to beside HBM bandwidth (on GB300 the

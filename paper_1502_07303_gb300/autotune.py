@@ -42,9 +42,12 @@ SEARCH = {
 }
 
 # A short list for a quick tune: the continuous schedule with a whole-brick
-# look-ahead over strides and bucket widths, at the full and at a reduced CTA
-# count, and the persistent schedule without restarts.
-QUICK = ([{"schedule": 3, "stride": s, "bucket": 4.0, "ahead": math.inf} for s in (0.5, 1.0, 2.0, 4.0)]
+# look-ahead over strides and bucket widths (around the fp64 optimum of 1 h
+# and the fp32 one of 2 h), at the full and at a reduced CTA count, and the
+# persistent schedule without restarts.
+QUICK = ([{"schedule": 3, "stride": s, "bucket": 4.0, "ahead": math.inf}
+          for s in (0.5, 1.0, 1.5, 2.0, 3.0, 4.0)]
+         + [{"schedule": 3, "stride": 1.0, "bucket": b, "ahead": math.inf} for b in (5.0, 6.0)]
          + [{"schedule": 3, "stride": 2.0, "bucket": b, "ahead": math.inf} for b in (3.0, 6.0)]
          + [{"schedule": 3, "stride": 1.0, "bucket": 4.0, "ahead": math.inf, "ctas": 152 * 4}]
          + [{"schedule": 2, "stride": math.inf, "bucket": 4.0}])

@@ -82,17 +82,20 @@ __device__ __forceinline__ dfl df_sqrt(dfl x)
     return df_fast_two_sum(s, res * (0.5f * r));
 }
 
-// x < y
+// x < y for normalized pairs (|l| at most half an ulp of h, as the
+// operations above return them): then the high parts decide unless they are
+// equal
 __device__ __forceinline__ bool df_lt(dfl x, dfl y)
 {
     return x.h < y.h || (x.h == y.h && x.l < y.l);
 }
 
-// A non-negative double of magnitude below 1e30 as a double-float: the high
-// part is the value truncated to 24 significant bits (fmm_fp64.cuh's f32_of),
-// the low part the remaining fraction bits as a float (the low 29 bits of the
-// double's fraction, of which the top 23 are kept), both built with integer
-// operations.  Values below 2^-100 become 0 (an absolute error no Algorithm
+// A non-negative double of magnitude below 1e30 as a double-float: the value
+// truncated to 24 significant bits (fmm_fp64.cuh's f32_of) plus the remaining
+// fraction bits as a float (the low 29 bits of the double's fraction, of which
+// the top 23 are kept), both built with integer operations.  The pair is not
+// normalized (lo may reach a whole ulp of hi), so df_lt against it can order
+// two values wrongly when they lie within a float ulp of each other.  Values below 2^-100 become 0 (an absolute error no Algorithm
 // 11 operand of order h notices).
 __device__ __forceinline__ dfl df_of(double v)
 {
@@ -124,9 +127,11 @@ __device__ __forceinline__ double df_to_double(dfl x)
 // sum_i (u - delta_i)^2 = q over the set: u = (S + sqrt(k q - P)) / k with
 // S = sum delta_i and P = sum_{i<j} (delta_i - delta_j)^2 (Lagrange's form of
 // S^2 - k (Q - q), a sum of squares, so nothing cancels), causal when the
-// largest delta is below u; the largest value is dropped while the set is not
+// largest delta is below u (kStrict: when the double root t = m + u exceeds
+// the largest value); the largest value is dropped while the set is not
 // causal.  Returns the number of values in the causal set (0: none, root
 // +inf) and the root in t.
+template <bool kStrict>
 __device__ __forceinline__ int df_shifted_root(double m, double v1, double v2, int nd, double q,
                                                double &t)
 {
@@ -151,10 +156,29 @@ __device__ __forceinline__ int df_shifted_root(double m, double v1, double v2, i
         if (disc.h > 0.0f) {
             const dfl r = df_add(S, df_sqrt(disc));
             const dfl u = nd == 3 ? df_mul(r, third) : (nd == 2 ? dfl{0.5f * r.h, 0.5f * r.l} : r);
-            const dfl dmax = nd == 3 ? D2 : D1;   // 0 when nd == 1
-            if (df_lt(dmax, u)) {
-                t = m + df_to_double(u);
-                return nd;
+            if constexpr (kStrict) {
+                // causal when the root exceeds the largest value of the set,
+                // tested on the doubles the cell and its neighbours will hold
+                // (the test on the shifted double-floats can pass by a
+                // rounding step while t rounds to that value or below it; an
+                // upwind set recorded for the adjoint must point strictly
+                // downhill)
+                const double tt = m + df_to_double(u);
+                const double vmax = nd == 3 ? v2 : v1;
+                if (nd == 1 || __double_as_longlong(vmax) < __double_as_longlong(tt)) {
+                    t = tt;
+                    return nd;
+                }
+            } else {
+                // without a recorded set, the shifted test suffices: it can
+                // err only where u and the largest delta lie within a float
+                // ulp of each other, and there the two sets' roots agree to
+                // about 1e-14 u
+                const dfl dmax = nd == 3 ? D2 : D1;   // 0 when nd == 1
+                if (df_lt(dmax, u)) {
+                    t = m + df_to_double(u);
+                    return nd;
+                }
             }
         }
         if (nd == 3)

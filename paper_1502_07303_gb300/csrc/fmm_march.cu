@@ -158,7 +158,10 @@ __device__ __forceinline__ float vsqrt(float v) { return v * rsqrtf(fmaxf(v, 1e-
 // m: t = m + u, delta_i = psi_i - m, sum_i (u - delta_i)^2 = q with
 // q = (h/F)^2.  The coefficients stay of order h, so rounding does not grow
 // with psi (in psi itself b^2 and 4ac would cancel to ~3 (psi F/h)^2 ulp).
-// The causality test psi_i < t is delta_i < u.  q is the cell's speed term.
+// The causality test psi_i < t is delta_i < u; the kernels that record the
+// upwind sets for the adjoint make it on t = m + u and the values the cells
+// hold (on rounded shifts delta_i < u can hold while t rounds to psi_i, and a
+// recorded set must point strictly downhill).  q is the cell's speed term.
 //
 // Per axis the upwind value is the smaller known neighbour if it is below
 // Tc; with a tape (kTape) the side it came from is kept as well (the minus
@@ -167,7 +170,8 @@ __device__ __forceinline__ float vsqrt(float v) { return v * rsqrtf(fmaxf(v, 1e-
 // first).  The smallest has delta = 0, so only the other two enter
 // S = sum delta_i and Q = sum delta_i^2 (a dropped axis contributes 0):
 // disc = S^2 - k (Q - q), u = (S + sqrt(disc)) / k, causal when the largest
-// remaining delta is below u.  All lanes of a warp evaluate their full set
+// remaining delta is below u (with a tape: when t = m + u exceeds the largest
+// remaining value).  All lanes of a warp evaluate their full set
 // together; a lane whose full set is not causal (about 1% of solves) goes
 // round the loop again.
 template <typename real>
@@ -223,7 +227,7 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
         // unless the speed term is outside its range (an obstacle's +inf)
         if (in_float_range(q)) {
             double t = 0.0;
-            const int k = df_shifted_root(v[0], v[1], v[2], nd, q, t);
+            const int k = df_shifted_root<kTape>(v[0], v[1], v[2], nd, q, t);
             if (k == 0)
                 return INF;
             set_out = (uint8_t)(code[0] | (k >= 2 ? code[1] : 0u) | (k == 3 ? code[2] : 0u));
@@ -241,10 +245,16 @@ __device__ __forceinline__ real solve_cell(const real *kv, int ti, real Tc, real
         if (!lt(disc, (real)0)) {
             const real inv_k = nd == 3 ? (real)(1.0 / 3.0) : (nd == 2 ? (real)0.5 : (real)1);
             const real u = (S + vsqrt(disc)) * inv_k;
-            const real dmax = nd == 3 ? d2 : d1;   // 0 when nd == 1
-            if (lt(dmax, u)) {
+            // causal: the largest remaining delta is below u; with a tape,
+            // the root above the largest value as the cells hold it (the
+            // upwind sets recorded for the adjoint must point strictly
+            // downhill); one value: u > 0
+            const real t = m + u;
+            const bool causal = kTape ? (nd == 1 ? lt((real)0, u) : lt(nd == 3 ? v[2] : v[1], t))
+                                      : lt(nd == 3 ? d2 : d1, u);
+            if (causal) {
                 set_out = (uint8_t)(code[0] | (nd >= 2 ? code[1] : 0u) | (nd == 3 ? code[2] : 0u));
-                return m + u;
+                return t;
             }
         }
         // drop the largest remaining value
@@ -281,7 +291,7 @@ __device__ __forceinline__ void cswap_w(real &a, real &wa, unsigned &ca, real &b
 __device__ __forceinline__ float vdiv(float a, float b) { return a / b; }
 __device__ __forceinline__ double vdiv(double a, double b) { return div_fp64(a, b); }
 
-template <typename real>
+template <typename real, bool kTape>
 __device__ __forceinline__ real solve_cell_w(const real *kv, int ti, real Tc, real q, real wy,
                                              real wz, uint8_t &set_out)
 {
@@ -326,10 +336,12 @@ __device__ __forceinline__ real solve_cell_w(const real *kv, int ti, real Tc, re
         const real disc = fma(K, q, -P);
         if (!lt(disc, (real)0)) {
             const real u = vdiv(S + vsqrt(disc), K);
-            const real dmax = nd == 3 ? d2 : d1;   // 0 when nd == 1
-            if (lt(dmax, u)) {
+            const real t = m + u;   // causal as in solve_cell
+            const bool causal = kTape ? (nd == 1 ? lt((real)0, u) : lt(nd == 3 ? v[2] : v[1], t))
+                                      : lt(nd == 3 ? d2 : d1, u);
+            if (causal) {
                 set_out = (uint8_t)(code[0] | (nd >= 2 ? code[1] : 0u) | (nd == 3 ? code[2] : 0u));
-                return m + u;
+                return t;
             }
         }
         // drop the largest remaining value with its weight
@@ -912,7 +924,7 @@ __device__ __forceinline__ void march_brick(const Geom &g, const DeviceState &s,
                 tc = kval(W.kv[ti]);
                 const real sp = kHetero ? __ldg(spd + base + c) : (real)spd_const_term;
                 if constexpr (kAniso)
-                    cand = solve_cell_w<real>(W.kv, ti, tc, sp, (real)p.wy, (real)p.wz, cset);
+                    cand = solve_cell_w<real, kTape>(W.kv, ti, tc, sp, (real)p.wy, (real)p.wz, cset);
                 else
                     cand = solve_cell<real, kTape>(W.kv, ti, tc, sp, cset);
             }

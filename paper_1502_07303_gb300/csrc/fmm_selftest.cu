@@ -1,8 +1,12 @@
 // fmm_selftest.cu -- fmm_selftest_fp64: the double-precision square root and
 // division helpers of fmm_fp64.cuh (used by the fp64 march and the adjoint)
 // evaluated element-wise on caller arrays, so that a test can compare them
-// with CUDA's correctly rounded sqrt and '/' over a sweep of operands.
+// with CUDA's correctly rounded sqrt and '/' over a sweep of operands;
+// fmm_selftest_root: the double-float root of Algorithm 11 used by the fp64
+// march, so that a test can check its causal set and root against exact
+// arithmetic; fmm_probe_fma_rate: the FMA throughput of the device.
 #include "fmm.h"
+#include "fmm_df.cuh"
 #include "fmm_fp64.cuh"
 
 #include <cuda_runtime.h>
@@ -32,6 +36,46 @@ extern "C" fmm_status fmm_selftest_fp64(const double *a, const double *b, double
     if (blocks > 152 * 16)
         blocks = 152 * 16;
     k_selftest_fp64<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, sqrt_out, div_out, n);
+    return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// The double-grid root of Algorithm 11 (fmm_df.cuh's df_shifted_root) on
+// caller arrays: sorted upwind values m <= v1 <= v2 (nd of them used), speed
+// term q; returns the root and the size of the causal set it chose.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_selftest_root(const double *__restrict__ m, const double *__restrict__ v1,
+                                const double *__restrict__ v2, const int *__restrict__ nd,
+                                const double *__restrict__ q, double *__restrict__ t_out,
+                                int *__restrict__ k_out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        // as the march computes it when it records the upwind sets
+        const int k = fmmgb::df_shifted_root<true>(m[i], v1[i], v2[i], nd[i], q[i], t);
+        t_out[i] = k ? t : __longlong_as_double(0x7ff0000000000000ll);
+        k_out[i] = k;
+    }
+}
+
+}  // namespace
+
+extern "C" fmm_status fmm_selftest_root(const double *m, const double *v1, const double *v2,
+                                        const int32_t *nd, const double *q, double *t_out,
+                                        int32_t *k_out, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!m || !v1 || !v2 || !nd || !q || !t_out || !k_out)))
+        return FMM_ERR_INVALID;
+    if (n == 0)
+        return FMM_OK;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    k_selftest_root<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(m, v1, v2, (const int *)nd, q, t_out,
+                                                                 (int *)k_out, n);
     return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
 }
 

@@ -24,7 +24,8 @@ EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_dista
             "fmm_adjoint", "fmm_get_stats", "fmm_last_error", "fmm_destroy",
             "fmm_reinit_signed_distance_noalloc", "fmm_create_batch", "fmm_reinit_batch",
             "fmm_get_trace", "fmm_resume", "fmm_checkpoint_size", "fmm_checkpoint_save",
-            "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch",
+            "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_selftest_root", "fmm_probe_fma_rate",
+            "fmm_solve_batch",
             "fmm_dd_start", "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers",
             "fmm_dd_integrate", "fmm_dd_finish")
 
@@ -112,12 +113,14 @@ def load(path: str | None = None):
     lib.fmm_checkpoint_save.argtypes = [vp, vp, i64]
     lib.fmm_checkpoint_load.argtypes = [vp, vp, i64]
     lib.fmm_selftest_fp64.argtypes = [vp, vp, vp, vp, i64, vp]
+    lib.fmm_selftest_root.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp]
     lib.fmm_probe_fma_rate.argtypes = [ctypes.c_int32, i64, ctypes.POINTER(dbl)]
     for n in ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_distance",
               "fmm_adjoint", "fmm_get_stats", "fmm_reinit_signed_distance_noalloc",
               "fmm_create_batch", "fmm_reinit_batch", "fmm_get_trace", "fmm_resume",
               "fmm_checkpoint_size", "fmm_checkpoint_save", "fmm_checkpoint_load",
-              "fmm_selftest_fp64", "fmm_probe_fma_rate", "fmm_solve_batch", "fmm_dd_start",
+              "fmm_selftest_fp64", "fmm_selftest_root", "fmm_probe_fma_rate", "fmm_solve_batch",
+              "fmm_dd_start",
               "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers", "fmm_dd_integrate",
               "fmm_dd_finish"):
         getattr(lib, n).restype = ctypes.c_int

@@ -365,6 +365,7 @@ def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream, params):
             times.append(e0.elapsed_time(e1))
     s.close()
     nbytes = phi_host.numel() * phi_host.element_size()
+    measure_e2e.step_ms = [round(t, 1) for t in times]
     return statistics.mean(times), nbytes, T_host.numel() * T_host.element_size()
 
 
@@ -679,7 +680,8 @@ def run_gpu(args):
                          if cpu_rate is not None else None),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "call": "fmm_reinit_signed_distance with pinned host phi0 and psi (fp64)"},
+                "call": "fmm_reinit_signed_distance with pinned host phi0 and psi (fp64)",
+                "step_ms": getattr(measure_e2e, "step_ms", None)},
         "gpu_launches": r64["launches"],
         "clocks": clocks,
         "fp32": {"value": total_pts / (ms32 / 1e3) / 1e9, "ms_per_step": ms32,

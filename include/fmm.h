@@ -358,8 +358,8 @@ void fmm_destroy(fmm_handle *hd);
  * about 2.4 MiB that every GPU loading the library holds until the process
  * exits.  Limit: at most 512 bricks of 8x8x8 cells (for example a 64^3 grid);
  * larger grids return FMM_ERR_INVALID.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  Later calls re-check the cached
+ * the array's device address (cudaGetSymbolAddress) and caches it.  Later
+ * calls re-check the cached
  * address (cudaPointerGetAttributes) and look it up again after a
  * cudaDeviceReset.  The call synchronises cfg->stream: it reads the restart
  * control block back between batches of restarts.  All calls on a device share the

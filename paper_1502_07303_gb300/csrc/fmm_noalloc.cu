@@ -15,8 +15,7 @@
 // The host cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so on the first call on each device, with that
 // device current, the address is looked up with cudaGetSymbolAddress and
-// cached; that first call should come before any stream capture.  Later calls
-// check the cached address with cudaPointerGetAttributes (which allocates
+// cached.  Later calls check the cached address with cudaPointerGetAttributes (which allocates
 // nothing) and look it up again if the device's context was reset since.
 // Every call on a device shares the same array, and the array keeps the
 // previous call's contents; everything the solve reads before writing
@@ -79,8 +78,7 @@ fmm_status cuda_error(cudaError_t e, const char *where)
 }
 
 // Device address of the scratch on the current device, looked up on the
-// first call on a device (make that call before any stream capture) and
-// cached.  A cached address that no longer names device memory of this
+// first call on a device and cached.  A cached address that no longer names device memory of this
 // device (the context was reset with cudaDeviceReset, which unloads and
 // reloads the module) is looked up again.
 fmm_status scratch_address(int dev, unsigned char **out)

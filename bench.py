@@ -46,6 +46,7 @@ ALG_BYTES = {"reinit": {"f32": 9, "f64": 17}, "sources": {"f32": 5, "f64": 9},
              "sources_speed": {"f32": 9, "f64": 17}}
 REF_SAMPLE_N = 192          # oracle sample grid of the reference arm
 CPU_BASELINE_N = 256        # oracle sample grid of the cpu_baseline entry
+CPU_BATCH_GRIDS = 48        # grids of the batched workload the oracle solves on all cores
 
 
 def peaks():
@@ -269,6 +270,23 @@ def oracle_rate(n):
     return p.n_points / dt / 1e9, dt
 
 
+def oracle_batch_rate(sample):
+    """The oracle on a sample of the batched workload's grids (the fp32 level
+    sets the batch solves, as (phi0, h) host pairs), one grid per thread on a
+    pool over all host cores; returns (Gpoints/s, s, cores, points)."""
+    import concurrent.futures
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as pool:
+        list(pool.map(lambda a: oracle.solve_reinit(a[0], a[1]), sample))
+    dt = time.perf_counter() - t0
+    pts = sum(a[0].size for a in sample)
+    return pts / dt / 1e9, dt, cores, pts
+
+
 def run_reference(args):
     ws, rank, local, pg = dist_setup()
     if rank != 0:
@@ -429,6 +447,9 @@ def measure_batch(fmm, torch, wl, autotune, stream, steps=2, warmup=1, tune=True
     probs = wl.batch(n_grids=256, lo=32, hi=192, seed=4, device="cuda")
     phis = [p.phi0.to(torch.float32).contiguous() for p in probs]
     pts = sum(p.n_points for p in probs)
+    # host copies of the first grids for the all-cores oracle baseline
+    measure_batch.sample = [(ph.double().cpu().numpy(), p.h) for ph, p in
+                            zip(phis[:CPU_BATCH_GRIDS], probs[:CPU_BATCH_GRIDS])]
     best, table = {}, []
     if tune:
         best, _, table = autotune.tune_batch(probs, torch.float32, search=autotune.QUICK, reps=2,
@@ -654,6 +675,13 @@ def run_gpu(args):
     wname = f"sphere{n}"
     k64, k32 = kernel_name(tuned["f64"]), kernel_name(tuned["f32"])
     cpu_rate, cpu_s = oracle_rate(CPU_BASELINE_N) if ws == 1 else (None, None)
+    if ws == 1 and "batched" in others:
+        # the batched workload's oracle on all host cores (a bounded sample)
+        r, t, cores, bpts = oracle_batch_rate(measure_batch.sample)
+        others["batched"]["cpu_baseline"] = {
+            "value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {CPU_BATCH_GRIDS} of the 256 grids ({bpts} points), one grid per "
+                      f"thread on a pool of {cores} host threads, oracle fp64, {t:.1f} s"}
     st = r64["stats"]
     st32 = r32["stats"]
     line = {

@@ -14,6 +14,8 @@ parallel fast marching method for the Eikonal equation"):
   bound = width (the sequential reference of Sec. 5.2), using Algorithm 10 and
   Algorithm 11
 * ``local_solve``                     -- Algorithm 11 on one cell
+* ``march(..., accuracy=2)``           -- the same march with second-order
+  one-sided differences (the higher-order variant of Sec. 6)
 * ``fast_sweep``                      -- an independent Gauss-Seidel solve of
   Eq. (2) (fast sweeping, cited in Sec. 1), used only to pin ``march``
 * ``adjoint`` / ``tangent``           -- derivatives of the discrete Eq. (2)
@@ -120,6 +122,10 @@ def _bind(lib):
                                  vp, vp, vp]
     lib.oracle_local_solve.argtypes = [vp, vp, dbl, vp, dbl]
     lib.oracle_local_solve.restype = dbl
+    lib.oracle_march_ho.argtypes = [i64, i64, i64, vp, vp, dbl, dbl, vp, vp,
+                                    vp, vp, ctypes.c_int]
+    lib.oracle_local_solve_ho.argtypes = [vp, vp, vp, vp, dbl, vp, dbl]
+    lib.oracle_local_solve_ho.restype = dbl
     lib.oracle_fast_sweep.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp,
                                       i64, vp]
     lib.oracle_adjoint.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp, vp,
@@ -127,7 +133,8 @@ def _bind(lib):
     lib.oracle_tangent.argtypes = [i64, i64, i64, vp, vp, dbl, vp, vp, vp,
                                    vp, i64, vp, vp]
     for name in ("oracle_init_sources", "oracle_init_reinit", "oracle_march",
-                 "oracle_fast_sweep", "oracle_adjoint", "oracle_tangent"):
+                 "oracle_march_ho", "oracle_fast_sweep", "oracle_adjoint",
+                 "oracle_tangent"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -182,11 +189,18 @@ def init_reinit(phi0, h):
     return T, G
 
 
-def march(T, G, h, speed=None, width=np.inf, record=False):
+def march(T, G, h, speed=None, width=np.inf, record=False, accuracy=1):
     """Algorithm 9 + Algorithm 12 (bound = width) in place on copies of T, G.
 
     Returns a dict with T, G and, when record=True, ``order`` (acceptance
-    sequence) and ``tape`` (upwind set of each cell's final root)."""
+    sequence) and ``tape`` (upwind set of each cell's final root).
+    ``accuracy=2`` uses second-order one-sided differences where the cell
+    beyond the upwind neighbour is known and monotone (no tape: the adjoint
+    linearises the first-order scheme)."""
+    if accuracy not in (1, 2):
+        raise ValueError("accuracy must be 1 or 2")
+    if accuracy == 2 and record:
+        raise ValueError("the tape records first-order upwind sets only")
     T = np.array(T, dtype=np.float64, order="C", copy=True)
     G = np.array(G, dtype=np.uint8, order="C", copy=True)
     nz, ny, nx = T.shape
@@ -196,9 +210,15 @@ def march(T, G, h, speed=None, width=np.inf, record=False):
     tape = np.empty(T.shape, np.uint8) if record else None
     n_order = ctypes.c_int64(0)
     h3 = _spacing(h)
-    _check(_load().oracle_march(nx, ny, nz, _ptr(h3), _ptr(sp), sc, float(width),
-                                _ptr(T), _ptr(G), _ptr(order),
-                                ctypes.addressof(n_order), _ptr(tape)), "march")
+    if accuracy == 1:
+        rc = _load().oracle_march(nx, ny, nz, _ptr(h3), _ptr(sp), sc, float(width),
+                                  _ptr(T), _ptr(G), _ptr(order),
+                                  ctypes.addressof(n_order), _ptr(tape))
+    else:
+        rc = _load().oracle_march_ho(nx, ny, nz, _ptr(h3), _ptr(sp), sc,
+                                     float(width), _ptr(T), _ptr(G), _ptr(order),
+                                     ctypes.addressof(n_order), 2)
+    _check(rc, "march")
     out = {"T": T, "G": G, "n_accepted": int(n_order.value)}
     if record:
         out["order"] = order[: n_order.value].copy()
@@ -216,14 +236,24 @@ def solve_reinit(phi0, h, speed=None, width=np.inf, record=False):
     return march(T, G, h, speed=speed, width=width, record=record)
 
 
-def local_solve(nb, nb_known, Tc, h, F):
-    """Algorithm 11 on one cell from its six neighbours (-x,+x,-y,+y,-z,+z)."""
+def local_solve(nb, nb_known, Tc, h, F, nb2=None, nb2_known=None):
+    """Algorithm 11 on one cell from its six neighbours (-x,+x,-y,+y,-z,+z).
+
+    With ``nb2`` (the cells two steps away in the same six directions) and
+    ``nb2_known``, the second-order variant of ``march(..., accuracy=2)``."""
     nb = np.ascontiguousarray(nb, dtype=np.float64)
     kn = np.ascontiguousarray(nb_known, dtype=np.uint8)
     assert nb.shape == (6,) and kn.shape == (6,)
     h3 = _spacing(h)
-    return float(_load().oracle_local_solve(_ptr(nb), _ptr(kn), float(Tc),
-                                            _ptr(h3), float(F)))
+    if nb2 is None:
+        return float(_load().oracle_local_solve(_ptr(nb), _ptr(kn), float(Tc),
+                                                _ptr(h3), float(F)))
+    nb2 = np.ascontiguousarray(nb2, dtype=np.float64)
+    kn2 = np.ascontiguousarray(nb2_known, dtype=np.uint8)
+    assert nb2.shape == (6,) and kn2.shape == (6,)
+    return float(_load().oracle_local_solve_ho(_ptr(nb), _ptr(kn), _ptr(nb2),
+                                               _ptr(kn2), float(Tc), _ptr(h3),
+                                               float(F)))
 
 
 def fast_sweep(A0, fixed, h, speed=None, max_rounds=10000):

@@ -14,6 +14,10 @@
  * negative indices.  Heap ties (equal |psi|) pop the smaller linear index
  * first; the paper is silent on ties.
  *
+ * oracle_march_ho adds the higher-order fast marching of Sec. 6 (future work
+ * there): the same march with second-order one-sided differences on the axes
+ * where the next cell beyond the upwind neighbour is known and monotone.
+ *
  * Build: plain C11, -ffp-contract=off so that no multiply-add is fused and
  * x86-64 and aarch64 produce the same bits.
  */
@@ -189,6 +193,7 @@ typedef struct {
     heap_t heap[2];     /* [0]: side -1, [1]: side +1 */
     int64_t *order;
     int64_t n_order;
+    int accuracy;       /* 1: Eq. (2)-(3); 2: second-order upwind differences */
 } march_t;
 
 static int heap_less(const march_t *m, int32_t a, int32_t b)
@@ -335,6 +340,24 @@ static double quadratic_roots(double psi[3], double hh[3], const int dir[3],
     return psi_temp;
 }
 
+/* Second-order upwind difference along one axis (the higher-order fast
+ * marching that Sec. 6 names as future work; the scheme is the textbook
+ * second-order FMM).  With psi1 the upwind neighbour and psi2 the next cell
+ * beyond it in the same direction, the one-sided difference
+ * (3 t - 4 psi1 + psi2) / (2 h) equals (3 / (2 h)) (t - (4 psi1 - psi2) / 3):
+ * the axis enters Algorithm 11's quadratic unchanged, with
+ * psi_i = (4 psi1 - psi2) / 3 and h_i = 3 / (2 h).  It is used only where
+ * psi2 is KNOWN and not above psi1 (the values fall monotonically away from
+ * the cell); otherwise the axis keeps the first-order difference. */
+static void second_order_axis(double psi1, double psi2, int known2, double h,
+                              double *psi, double *hh)
+{
+    if (known2 && psi2 <= psi1) {
+        *psi = (4.0 * psi1 - psi2) / 3.0;
+        *hh = 3.0 / (2.0 * h);
+    }
+}
+
 static double solve_quadratic(const march_t *m, int64_t l, uint8_t *set_out)
 {
     const grid_t *g = &m->g;
@@ -359,6 +382,14 @@ static double solve_quadratic(const march_t *m, int64_t l, uint8_t *set_out)
         if (d != 0) {
             psi[a] = fabs(m->T[l + d * g->stride[a]]);
             hh[a] = 1.0 / m->h3[a];
+            if (m->accuracy == 2) {
+                int64_t c1[3] = {c[0], c[1], c[2]};
+                c1[a] += d;
+                int64_t q2 = grid_nb(g, l + d * g->stride[a], c1, a, d);
+                if (q2 >= 0)
+                    second_order_axis(psi[a], fabs(m->T[q2]), is_known(m->G[q2]),
+                                      m->h3[a], &psi[a], &hh[a]);
+            }
         } else {
             psi[a] = 0.0;
             hh[a] = 0.0;
@@ -393,6 +424,38 @@ double oracle_local_solve(const double nb[6], const uint8_t nb_known[6],
         } else {
             psi[a] = 0.0;
             hh[a] = 0.0;
+        }
+    }
+    return quadratic_roots(psi, hh, dir, 1.0 / (F * F), NULL);
+}
+
+double oracle_local_solve_ho(const double nb[6], const uint8_t nb_known[6],
+                             const double nb2[6], const uint8_t nb2_known[6],
+                             double Tc, const double h3[3], double F)
+{
+    double psi[3], hh[3];
+    int dir[3];
+    double Tl = fabs(Tc);
+    for (int a = 0; a < 3; ++a) {
+        int d = 0;
+        double vm = fabs(nb[2 * a]), vp = fabs(nb[2 * a + 1]);
+        if (nb_known[2 * a] && vm < Tl)
+            d = -1;
+        if (nb_known[2 * a + 1] && vp < Tl) {
+            if (d == 0)
+                d = 1;
+            else if (vp < vm)
+                d = 1;
+        }
+        dir[a] = d;
+        psi[a] = 0.0;
+        hh[a] = 0.0;
+        if (d != 0) {
+            int q = 2 * a + (d < 0 ? 0 : 1);
+            psi[a] = fabs(nb[q]);
+            hh[a] = 1.0 / h3[a];
+            second_order_axis(psi[a], fabs(nb2[q]), nb2_known[q] != 0, h3[a],
+                              &psi[a], &hh[a]);
         }
     }
     return quadratic_roots(psi, hh, dir, 1.0 / (F * F), NULL);
@@ -446,15 +509,16 @@ static int update_neighbors(march_t *m, int64_t idx, int s)
 /* Algorithm 9 + Algorithm 12 with bound = width                              */
 /* ------------------------------------------------------------------------ */
 
-int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
-                 const double *speed, double speed_const, double width,
-                 double *T, uint8_t *G,
-                 int64_t *order, int64_t *n_order, uint8_t *tape)
+static int march_run(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
+                     const double *speed, double speed_const, double width,
+                     double *T, uint8_t *G,
+                     int64_t *order, int64_t *n_order, uint8_t *tape, int accuracy)
 {
     march_t m;
     memset(&m, 0, sizeof(m));
     if (grid_make(&m.g, nx, ny, nz) || !T || !G || !spacing_ok(h3))
         return -1;
+    m.accuracy = accuracy;
     if (m.g.n >= (int64_t)2147483647)
         return -1;
     if (!speed && !(speed_const > 0))
@@ -515,6 +579,26 @@ int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
     free(m.heap[0].a);
     free(m.heap[1].a);
     return rc;
+}
+
+int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
+                 const double *speed, double speed_const, double width,
+                 double *T, uint8_t *G,
+                 int64_t *order, int64_t *n_order, uint8_t *tape)
+{
+    return march_run(nx, ny, nz, h3, speed, speed_const, width, T, G, order,
+                     n_order, tape, 1);
+}
+
+int oracle_march_ho(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
+                    const double *speed, double speed_const, double width,
+                    double *T, uint8_t *G,
+                    int64_t *order, int64_t *n_order, int accuracy)
+{
+    if (accuracy != 1 && accuracy != 2)
+        return -1;
+    return march_run(nx, ny, nz, h3, speed, speed_const, width, T, G, order,
+                     n_order, NULL, accuracy);
 }
 
 /* ------------------------------------------------------------------------ */

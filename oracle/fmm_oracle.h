@@ -73,6 +73,26 @@ int oracle_march(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
 double oracle_local_solve(const double nb[6], const uint8_t nb_known[6],
                           double Tc, const double h3[3], double F);
 
+/* The higher-order fast marching that Sec. 6 names as future work, with the
+ * restarted-band march unchanged: oracle_march with accuracy 2 replaces the
+ * first-order difference on an upwind axis by the second-order one-sided
+ * difference (3 t - 4 psi1 + psi2) / (2 h) wherever the cell psi2 two steps
+ * away on that side is KNOWN and |psi2| <= |psi1|; elsewhere, and everywhere
+ * for accuracy 1, the axis is first order as in Eq. (2)-(3).  No tape: the
+ * adjoint and tangent below linearise the first-order scheme only.  Returns
+ * -1 for an accuracy other than 1 or 2. */
+int oracle_march_ho(int64_t nx, int64_t ny, int64_t nz, const double h3[3],
+                    const double *speed, double speed_const, double width,
+                    double *T, uint8_t *G,
+                    int64_t *order, int64_t *n_order, int accuracy);
+
+/* oracle_local_solve with the second-order difference of oracle_march_ho:
+ * nb2[q] / nb2_known[q] are the cells two steps away in the same six
+ * directions. */
+double oracle_local_solve_ho(const double nb[6], const uint8_t nb_known[6],
+                             const double nb2[6], const uint8_t nb2_known[6],
+                             double Tc, const double h3[3], double F);
+
 /* Gauss-Seidel fast sweeping (Zhao 2005, cited in Sec. 1) with the textbook
  * sorted Godunov update of Eq. (2) over all six neighbours (the per-axis
  * minima sorted together with their cell sizes).  A holds |psi|:

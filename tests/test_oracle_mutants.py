@@ -16,6 +16,10 @@ _spec = importlib.util.spec_from_file_location(
     "oracle_pins", os.path.join(_HERE, "test_oracle_pins.py"))
 pins = importlib.util.module_from_spec(_spec)
 _spec.loader.exec_module(pins)
+_spec2 = importlib.util.spec_from_file_location(
+    "oracle_second_order", os.path.join(_HERE, "test_oracle_second_order.py"))
+so = importlib.util.module_from_spec(_spec2)
+_spec2.loader.exec_module(so)
 
 MUTANTS = {
     "discriminant_sign": ("double disc = qb * qb - (4.0 * qa) * qc;",
@@ -46,6 +50,19 @@ MUTANTS = {
     "adjoint_weight_wrong_axis": ("D += (Tp - fabs(T[nbr[q]])) * w[ax[q]];",
                                   "D += (Tp - fabs(T[nbr[q]])) * w[0];"),
     "tangent_sign": ("dT[p] = (sp * v[p] + acc) / D;", "dT[p] = (sp * v[p] - acc) / D;"),
+    # the second-order variant
+    "ho_extrapolation": ("*psi = (4.0 * psi1 - psi2) / 3.0;",
+                         "*psi = (3.0 * psi1 - psi2) / 2.0;"),
+    "ho_weight": ("*hh = 3.0 / (2.0 * h);", "*hh = 2.0 / (3.0 * h);"),
+    "ho_no_monotone_test": ("if (known2 && psi2 <= psi1) {", "if (known2) {"),
+    "ho_no_known_test": ("if (known2 && psi2 <= psi1) {", "if (psi2 <= psi1) {"),
+    "ho_second_cell_direction": (
+        "int64_t q2 = grid_nb(g, l + d * g->stride[a], c1, a, d);",
+        "int64_t q2 = grid_nb(g, l + d * g->stride[a], c1, a, -d);"),
+    "ho_cell_size_wrong_axis": ("m->h3[a], &psi[a], &hh[a]);",
+                                "m->h3[0], &psi[a], &hh[a]);"),
+    "ho_local_side": ("int q = 2 * a + (d < 0 ? 0 : 1);",
+                      "int q = 2 * a + (d < 0 ? 1 : 0);"),
 }
 
 PINS = [
@@ -65,6 +82,12 @@ PINS = [
     (pins.test_anisotropic_oblique_plane_front_exact, {}),
     (pins.test_anisotropic_residual_and_fast_sweep, {"seed": 7, "shape": (9, 13, 7)}),
     (pins.test_anisotropic_adjoint_finite_differences, {}),
+    (so.test_second_order_local_solve_closed_forms, {}),
+    (so.test_second_order_mixed_axes_against_np_roots, {}),
+    (so.test_second_order_falls_back_to_first_order, {}),
+    (so.test_second_order_slab_is_exact, {}),
+    (so.test_second_order_bowl_is_exact, {"h3": (1 / 20, 1.5 / 20, 0.75 / 20)}),
+    (so.test_second_order_convergence, {}),
 ]
 
 

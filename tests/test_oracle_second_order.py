@@ -1,0 +1,189 @@
+"""Pins for the oracle's second-order march (the higher-order fast marching
+that Sec. 6 of the paper names as future work; the scheme is the textbook
+second-order FMM: on an upwind axis whose next cell beyond the neighbour is
+known and not above it, the one-sided difference (3 t - 4 psi1 + psi2)/(2h)
+replaces (t - psi1)/h).
+
+Each check comes from the mathematics, not from the oracle's own formula:
+
+* closed forms of the local solve, derived by hand from the one-sided
+  difference equation, and mixed first/second-order roots from np.roots
+* a second neighbour that is unknown, non-monotone or on the other side
+  leaves the first-order local solve unchanged, bit for bit
+* one-sided second-order differences are exact for quadratics: a slab with
+  slowness 1 + x (T = x + x^2/2, the BDF2 recurrence) and the bowl
+  T = |x|^2 / 2 with slowness |x| (isotropic and with cells of unequal
+  sides) are reproduced to rounding, where the first-order march errs by O(h)
+* away from a point source with exact values inside a ball, the error falls
+  by about 4 per halving of h (first order: about 2)
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def _ho(oracle, nb, kn, nb2, kn2, Tc=np.inf, h=1.0, F=1.0):
+    return oracle.local_solve(np.array(nb, float), np.array(kn, np.uint8), Tc, h, F,
+                              nb2=np.array(nb2, float), nb2_known=np.array(kn2, np.uint8))
+
+
+INF = np.inf
+
+
+def test_second_order_local_solve_closed_forms(oracle):
+    # one axis: (3 t - 4 a + b) / (2 h) = 1/F
+    for a, b, h, F in [(1.0, 0.0, 1.0, 1.0), (2.5, 1.75, 0.5, 2.0), (0.3, 0.3, 0.1, 0.7)]:
+        t = _ho(oracle, [a, INF, INF, INF, INF, INF], [1, 0, 0, 0, 0, 0],
+                [b, 0, 0, 0, 0, 0], [1, 0, 0, 0, 0, 0], h=h, F=F)
+        assert t == pytest.approx((4 * a - b + 2 * h / F) / 3, rel=1e-15, abs=1e-15)
+        # the same from the plus side
+        t = _ho(oracle, [INF, a, INF, INF, INF, INF], [0, 1, 0, 0, 0, 0],
+                [0, b, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0], h=h, F=F)
+        assert t == pytest.approx((4 * a - b + 2 * h / F) / 3, rel=1e-15, abs=1e-15)
+    # three equal axes: 3 ((3 t - 4 a + b) / (2 h))^2 = F^-2
+    a, b, h, F = 1.0, 0.8, 0.25, 1.3
+    nb = [a, INF, INF, a, a, INF]
+    kn = [1, 0, 0, 1, 1, 0]
+    nb2 = [b, 0, 0, b, b, 0]
+    t = _ho(oracle, nb, kn, nb2, kn, h=h, F=F)
+    assert t == pytest.approx((4 * a - b + 2 * h / (math.sqrt(3.0) * F)) / 3, rel=1e-14)
+
+
+def test_second_order_mixed_axes_against_np_roots(oracle):
+    # x second order (a, b), y first order (c): the larger root of
+    # ((3t - 4a + b)/(2 hx))^2 + ((t - c)/hy)^2 = F^-2
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        hx, hy = rng.uniform(0.5, 2.0, size=2)
+        F = rng.uniform(0.5, 2.0)
+        a = rng.uniform(1.0, 1.2)
+        b = rng.uniform(0.0, a)   # |b| <= a: the x axis is second order
+        c = a + rng.uniform(-0.3, 0.3) * hy / F
+        ex = (3.0 / (2 * hx)) ** 2
+        ey = 1.0 / hy ** 2
+        e0 = (4 * a - b) / 3
+        coef = [ex + ey, -2 * (ex * e0 + ey * c), ex * e0 * e0 + ey * c * c - 1 / F ** 2]
+        r = np.roots(coef)
+        r = r[np.isreal(r)].real
+        cands = [x for x in r if x > e0 and x > c]
+        # one-axis roots for the causal fallback
+        cands.append(e0 + (2 * hx / 3) / F)
+        cands.append(c + hy / F)
+        expect = min(cands)
+        t = _ho(oracle, [a, INF, c, INF, INF, INF], [1, 0, 1, 0, 0, 0],
+                [b, 0, 0, 0, 0, 0], [1, 0, 0, 0, 0, 0], h=(hx, hy, 1.0), F=F)
+        assert t == pytest.approx(expect, rel=1e-12)
+
+
+def test_second_order_falls_back_to_first_order(oracle):
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        nb = rng.uniform(0.0, 1.0, size=6)
+        kn = rng.integers(0, 2, size=6).astype(np.uint8)
+        h = tuple(rng.uniform(0.5, 1.5, size=3))
+        F = rng.uniform(0.5, 2.0)
+        first = oracle.local_solve(nb, kn, np.inf, h, F)
+        # second neighbours unknown, whatever their values
+        t = oracle.local_solve(nb, kn, np.inf, h, F, nb2=nb - 0.5,
+                               nb2_known=np.zeros(6, np.uint8))
+        assert t == first
+        # second neighbours known but above the first ones (not monotone)
+        t = oracle.local_solve(nb, kn, np.inf, h, F, nb2=nb + 0.25,
+                               nb2_known=np.ones(6, np.uint8))
+        assert t == first
+    # a known, monotone second neighbour on the side that is not upwind
+    nb = [0.5, 0.75, INF, INF, INF, INF]
+    kn = [1, 1, 0, 0, 0, 0]
+    t = _ho(oracle, nb, kn, [0, 0.0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0])
+    assert t == oracle.local_solve(np.array(nb), np.array(kn, np.uint8), np.inf, 1.0, 1.0)
+    assert t == 1.5
+
+
+def _fix(T_exact, mask, oracle):
+    T = np.where(mask, T_exact, np.inf)
+    G = np.where(mask, oracle.KNOWN_FIX, oracle.FAR).astype(np.uint8)
+    return T, G
+
+
+def test_second_order_slab_is_exact(oracle):
+    """Slowness 1 + x along x only: T = x + x^2/2.  The second-order march is
+    the BDF2 recurrence, exact for quadratics; the first-order one errs by
+    O(h)."""
+    n, h = 48, 1.0 / 48
+    x = np.arange(n) * h
+    T_ex = np.broadcast_to(x + 0.5 * x * x, (3, 4, n)).copy()
+    F = np.broadcast_to(1.0 / (1.0 + x), (3, 4, n)).copy()
+    mask = np.zeros(T_ex.shape, bool)
+    mask[..., :2] = True
+    T, G = _fix(T_ex, mask, oracle)
+    r2 = oracle.march(T, G, h, speed=F, accuracy=2)
+    r1 = oracle.march(T, G, h, speed=F)
+    assert np.abs(r2["T"] - T_ex).max() <= 1e-13
+    assert np.abs(r1["T"] - T_ex).max() > 1e-3
+    assert np.all(r2["G"] == np.where(mask, oracle.KNOWN_FIX, oracle.KNOWN_NEW))
+
+
+@pytest.mark.parametrize("h3", [(1 / 20, 1 / 20, 1 / 20), (1 / 20, 1.5 / 20, 0.75 / 20)])
+def test_second_order_bowl_is_exact(oracle, h3):
+    """T = |x|^2 / 2 with slowness |x| on x, y, z > 0: every upwind axis has a
+    known monotone second neighbour once the two layers at the low faces are
+    fixed, and one-sided second-order differences are exact for quadratics,
+    with each axis's own cell size."""
+    n = 20
+    coords = [(np.arange(n) + 1.0) * h for h in h3]
+    Z, Y, X = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+    T_ex = 0.5 * (X * X + Y * Y + Z * Z)
+    F = 1.0 / np.sqrt(X * X + Y * Y + Z * Z)
+    mask = np.indices((n, n, n)).min(axis=0) < 2
+    T, G = _fix(T_ex, mask, oracle)
+    r2 = oracle.march(T, G, h3, speed=F, accuracy=2)
+    r1 = oracle.march(T, G, h3, speed=F)
+    err2 = np.abs(r2["T"] - T_ex).max() / T_ex.max()
+    err1 = np.abs(r1["T"] - T_ex).max() / T_ex.max()
+    assert err2 <= 1e-13
+    assert err1 > 1e-2
+
+
+def _point_errors(oracle, n, accuracy, R0=0.25):
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    R = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    mask = R < R0
+    T, G = _fix(R, mask, oracle)
+    e = np.abs(oracle.march(T, G, h, accuracy=accuracy)["T"] - R)[~mask]
+    return e.max(), e.mean()
+
+
+def test_second_order_convergence(oracle):
+    """Distance from a point with exact values inside a ball of radius 1/4:
+    halving h divides the error by about 4 (second order) instead of about 2
+    (first order)."""
+    m24, a24 = _point_errors(oracle, 24, 2)
+    m48, a48 = _point_errors(oracle, 48, 2)
+    assert m24 / m48 > 3.2 and a24 / a48 > 3.2
+    f24, _ = _point_errors(oracle, 24, 1)
+    f48, _ = _point_errors(oracle, 48, 1)
+    assert 1.6 < f24 / f48 < 2.4
+    assert m48 < f48 / 10
+
+
+def test_second_order_arguments(oracle):
+    T, G = oracle.init_sources((4, 4, 4), [(1, 1, 1)])
+    with pytest.raises(ValueError):
+        oracle.march(T, G, 1.0, accuracy=3)
+    with pytest.raises(ValueError):
+        oracle.march(T, G, 1.0, accuracy=2, record=True)
+    # accuracy 1 through the second entry point is the first-order march
+    a = oracle.march(T, G, 1.0)
+    lib = oracle._load()
+    T1 = T.copy()
+    G1 = G.copy()
+    h3 = np.ones(3)
+    rc = lib.oracle_march_ho(4, 4, 4, h3.ctypes.data, None, 1.0, np.inf,
+                             T1.ctypes.data, G1.ctypes.data, None, None, 1)
+    assert rc == 0 and np.array_equal(T1, a["T"]) and np.array_equal(G1, a["G"])
+    rc = lib.oracle_march_ho(4, 4, 4, h3.ctypes.data, None, 1.0, np.inf,
+                             T1.ctypes.data, G1.ctypes.data, None, None, 0)
+    assert rc == -1

@@ -187,3 +187,79 @@ def test_second_order_arguments(oracle):
     rc = lib.oracle_march_ho(4, 4, 4, h3.ctypes.data, None, 1.0, np.inf,
                              T1.ctypes.data, G1.ctypes.data, None, None, 0)
     assert rc == -1
+
+
+def _bucketed_march(oracle, T0, G0, h, delta, accuracy):
+    """A bucketed, label-correcting march (all BAND cells within delta of the
+    band minimum accepted together, every non-FIX neighbour of an accepted
+    cell re-solved, a cell whose value drops becomes BAND again), written
+    here with the oracle's local solve: the order of updates a data-parallel
+    march uses instead of the heap."""
+    T = T0.copy()
+    fix = G0 == oracle.KNOWN_FIX
+    known = fix.copy()
+    shape = T.shape
+    steps = [(0, 0, 1), (0, 1, 0), (1, 0, 0)]   # x, y, z in (k, j, i)
+
+    def inside(q):
+        return all(0 <= q[a] < shape[a] for a in range(3))
+
+    def solve(p):
+        nb, kn = np.full(6, np.inf), np.zeros(6, np.uint8)
+        nb2, kn2 = np.zeros(6), np.zeros(6, np.uint8)
+        for ax, d in enumerate(steps):
+            for si, s in enumerate((-1, 1)):
+                q = tuple(p[a] + s * d[a] for a in range(3))
+                q2 = tuple(p[a] + 2 * s * d[a] for a in range(3))
+                if inside(q):
+                    nb[2 * ax + si], kn[2 * ax + si] = T[q], known[q]
+                if inside(q2):
+                    nb2[2 * ax + si], kn2[2 * ax + si] = T[q2], known[q2]
+        if accuracy == 1:
+            return oracle.local_solve(nb, kn, T[p], h, 1.0)
+        return oracle.local_solve(nb, kn, T[p], h, 1.0, nb2=nb2, nb2_known=kn2)
+
+    def relax(p):
+        for d in steps:
+            for s in (-1, 1):
+                q = tuple(p[a] + s * d[a] for a in range(3))
+                if inside(q) and not fix[q]:
+                    t = solve(q)
+                    if t < T[q]:
+                        T[q] = t
+                        known[q] = False
+
+    for p in zip(*np.nonzero(fix)):
+        relax(p)
+    while True:
+        band = ~known & np.isfinite(T)
+        if not band.any():
+            return T
+        acc = band & (T <= T[band].min() + delta)
+        known |= acc
+        for p in zip(*np.nonzero(acc)):
+            relax(p)
+
+
+def test_second_order_result_depends_on_the_update_order(oracle):
+    """Sec. 5.2's agreement of parallel and sequential marches rests on the
+    first-order scheme having one discrete solution whatever the update
+    order: a bucketed label-correcting march reproduces the heap march bit
+    for bit.  The second-order update is not monotone in its operands, so the
+    same bucketed march reaches another solution, as accurate but different
+    cell by cell (the reason the second-order variant has no GPU kernel held
+    to the oracle)."""
+    n = 10
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    R = np.sqrt((X - 0.3) ** 2 + (Y - 0.4) ** 2 + (Z - 0.5) ** 2)
+    T0, G0 = _fix(R, R < 0.2, oracle)
+    seq1 = oracle.march(T0, G0, h)["T"]
+    seq2 = oracle.march(T0, G0, h, accuracy=2)["T"]
+    for delta in (0.0, 2 * h):
+        assert np.array_equal(_bucketed_march(oracle, T0, G0, h, delta, 1), seq1)
+        lc2 = _bucketed_march(oracle, T0, G0, h, delta, 2)
+        assert np.abs(lc2 - seq2).max() > 1e-4
+        err_seq, err_lc = np.abs(seq2 - R).max(), np.abs(lc2 - R).max()
+        assert err_lc < 1.5 * err_seq

@@ -78,7 +78,10 @@ typedef struct {
                               cluster and tuning per platform, Sec. 5.5);
                               +inf allowed                                     */
     double bucket;         /* accepted bucket width inside a brick, in units of
-                              h * min(1/F) / sqrt(3); 0 -> 4; +inf allowed     */
+                              h * min(1/F) / sqrt(3); 0 -> 4 (0.6 for the
+                              second-order march, whose accepted values must
+                              be final when their neighbours read them: see
+                              accuracy); +inf allowed                        */
     int32_t ctas;          /* CTAs of the march kernel; 0 -> as many as fit     */
     int32_t timeout_s;     /* host wall-clock limit of one solve in seconds;
                               0 -> 600; exceeding it returns FMM_ERR_TIMEOUT  */
@@ -89,7 +92,8 @@ typedef struct {
     int32_t exchange_passes; /* phased schedule: exchange + march passes after
                               the first march of every restart (Algorithm 16
                               has 1); 0 -> 2 for FMM_F32, 1 for FMM_F64      */
-    int32_t schedule;      /* 0 -> continuous (the default); 1 phased: every
+    int32_t schedule;      /* 0 -> continuous (the default; cell-parallel when
+                              accuracy is 2); 1 phased: every
                               restart is a select + march launch, then
                               exchange_passes select + march launches, as in
                               Algorithm 16; 2 persistent: one launch per
@@ -98,7 +102,17 @@ typedef struct {
                               is left; 3 continuous: one launch for the whole
                               solve, the bound rises by the stride whenever
                               few bricks are left below it, so one restart's
-                              last bricks overlap the next one's first      */
+                              last bricks overlap the next one's first; 4
+                              cell-parallel: no bricks or restarts, every
+                              bucket step accepts the BAND cells within the
+                              bucket of each side's minimum over the whole
+                              grid and re-solves their neighbours (Jacobi
+                              within the step, corrections as in the brick
+                              march), three grid-wide launches per step; no
+                              tape, no resume (max_restarts limits the
+                              steps); the schedule of the second-order march
+                              and, in first order, the same solution as the
+                              others (one discrete solution, Sec. 5.2)      */
     int32_t max_lead;      /* continuous schedule: while bricks are queued or
                               marching, the bound stays within max_lead
                               strides of the smallest BAND value the last scan
@@ -136,12 +150,34 @@ typedef struct {
                               for FMM_F64 in this mode.  Single grids only (not batches, the
                               fmm_dd_* entry points or the entry point
                               without allocation).  0 normally.             */
+    int32_t accuracy;      /* 0 or 1: the first-order upwind scheme of Eq.
+                              (2)-(3).  2: the higher-order fast marching of
+                              Sec. 6 (future work there), in the textbook
+                              second-order form: on an upwind axis whose
+                              next cell beyond the neighbour psi1, in the
+                              same direction, is known with psi2 <= psi1,
+                              the one-sided difference (3 t - 4 psi1 +
+                              psi2) / (2 h) replaces (t - psi1) / h.  Needs
+                              schedule 0 or 4 (runs the cell-parallel
+                              schedule), record_tape 0, deterministic 0;
+                              single grids only.  The second-order update is
+                              not monotone in its operands (a larger psi2
+                              lowers the root), so the result depends on the
+                              order of acceptances and in general differs,
+                              within the discretisation error, from the
+                              sequential heap march's; buckets above 2/3 let
+                              a value that is still being lowered serve as a
+                              second neighbour and cost accuracy.  Quadratic
+                              solutions are reproduced to rounding, and runs
+                              are reproducible.                             */
 } fmm_config;
 
 /* Statistics of the last solve on a handle. */
 typedef struct {
     int64_t restarts;        /* passes of the Algorithm 16 loop, including the
-                                final one that only tests for termination      */
+                                final one that only tests for termination
+                                (schedule 4: bucket steps that accepted
+                                cells; its brick counters stay 0)             */
     int64_t brick_marches;   /* local marches of a brick (both phases)           */
     int64_t march_rounds;    /* bucket rounds summed over all brick marches      */
     int64_t exchanges;       /* brick faces that sent changed overlap data       */
@@ -177,6 +213,24 @@ typedef struct fmm_handle fmm_handle;
  */
 fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_const,
                       const int64_t *src_ijk, int64_t n_src, fmm_handle **out);
+
+/*
+ * fmm_solve_fixed -- solve from given interface values (Algorithm 8 with the
+ * values of the interface cells supplied by the caller instead of computed
+ * from a level set or point sources; then Algorithms 9-12/16 as fmm_solve).
+ *   T0       : nx*ny*nz values (dtype, x-fastest, device or host, 16-byte
+ *              aligned).  A finite value makes the cell KNOWN_FIX with psi =
+ *              T0 on the side of its sign (v < 0: side -1; +0 and -0 are
+ *              side +1); +inf / -inf marks a FAR cell of side +1 / -1.  As in
+ *              Algorithm 8, both cells of every sign change between
+ *              6-neighbours must be finite.
+ *   T_out    : as fmm_solve.   tags_out : as fmm_solve (may be NULL).
+ * Returns FMM_ERR_INVALID for a NaN in T0 or a sign change between two
+ * cells that are not both finite (nothing solved), else as fmm_solve.  The
+ * call synchronises the stream once after the initialisation to read that
+ * check.
+ */
+fmm_status fmm_solve_fixed(fmm_handle *hd, const void *T0, void *T_out, uint8_t *tags_out);
 
 /*
  * fmm_set_speed -- replace the speed field of an existing handle (same rules

@@ -20,7 +20,8 @@ LIB_NAME = "libfmm_gb300.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fmm_api.cu", "fmm_march.cu", "fmm_adjoint.cu", "fmm_noalloc.cu", "fmm_selftest.cu"]
+SOURCES = ["fmm_api.cu", "fmm_march.cu", "fmm_adjoint.cu", "fmm_noalloc.cu", "fmm_selftest.cu",
+           "fmm_cell.cu"]
 
 
 def _nvcc():

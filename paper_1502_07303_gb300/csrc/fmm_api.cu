@@ -54,6 +54,10 @@ struct fmm_handle {
     long long *d_bsrc = nullptr;       // batch sources, 4 per source (grid, i, j, k)
     size_t bsrc_cap = 0;               // sources d_bsrc holds
     bool batch_speed_const1 = true;    // the speed terms on the device are F = 1
+    // cell-parallel march (schedule 4): the step's new values (brick
+    // layout) and two slots of the per-side BAND minima
+    void *cell_next = nullptr;
+    unsigned long long *cell_min = nullptr;
     std::string err;
 };
 
@@ -139,6 +143,12 @@ void free_state(fmm_handle *hd)
     if (hd->stage_tags)
         cudaFree(hd->stage_tags);
     hd->stage_tags = nullptr;
+    if (hd->cell_next)
+        cudaFree(hd->cell_next);
+    if (hd->cell_min)
+        cudaFree(hd->cell_min);
+    hd->cell_next = nullptr;
+    hd->cell_min = nullptr;
     memset(&hd->st, 0, sizeof(hd->st));
     hd->d_src = nullptr;
     hd->h_ctrl = nullptr;
@@ -240,10 +250,13 @@ fmm_status load_speed(fmm_handle *hd, const void *speed, double speed_const)
 }
 
 fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long long launches);
+fmm_status run_cell(fmm_handle *hd, void *T_out, uint8_t *tags_out);
 
 // Algorithm 9, then the loop of Algorithm 16, then the output conversion.
 fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
 {
+    if (hd->params.schedule == kScheduleCell)
+        return run_cell(hd, T_out, tags_out);
     DeviceState &s = hd->st;
     const Geom &g = hd->geom;
     const int dt = hd->cfg.dtype;
@@ -257,6 +270,42 @@ fmm_status run_solve(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     FMM_CUDA(hd, cudaMemsetAsync(s.queued, 0, (size_t)g.nbricks * sizeof(unsigned), st));
     FMM_CUDA(hd, launch_front_init(dt, g, s, hd->params, st));
     return run_restarts(hd, T_out, tags_out, 2);   // control reset, front init
+}
+
+// The output conversion into the caller's arrays (device memory, or host
+// memory through the staging buffers), then a synchronisation of the stream.
+fmm_status write_outputs(fmm_handle *hd, void *T_out, uint8_t *tags_out, long long &launches)
+{
+    DeviceState &s = hd->st;
+    const Geom &g = hd->geom;
+    const int dt = hd->cfg.dtype;
+    cudaStream_t st = hd->stream;
+    if (T_out) {
+        // host outputs go through the staging buffers (the input the first
+        // one held was consumed by the initialisation, earlier on the stream)
+        const bool host_T = is_host(T_out), host_G = tags_out && is_host(tags_out);
+        void *Td = T_out;
+        uint8_t *Gd = tags_out;
+        if (host_T) {
+            const fmm_status r = stage_buffer(hd, 0, &Td);
+            if (r != FMM_OK)
+                return r;
+        }
+        if (host_G) {
+            if (!hd->stage_tags)
+                FMM_CUDA(hd, alloc(&hd->stage_tags, natural_cells(hd)));
+            Gd = hd->stage_tags;
+        }
+        FMM_CUDA(hd, launch_output(dt, g, s, Td, Gd, st));
+        launches += 1;
+        if (host_T)
+            FMM_CUDA(hd, cudaMemcpyAsync(T_out, Td, natural_cells(hd) * hd->rsize,
+                                         cudaMemcpyDeviceToHost, st));
+        if (host_G)
+            FMM_CUDA(hd, cudaMemcpyAsync(tags_out, Gd, natural_cells(hd), cudaMemcpyDeviceToHost, st));
+    }
+    FMM_CUDA(hd, cudaStreamSynchronize(st));
+    return FMM_OK;
 }
 
 // The loop of Algorithm 16 from the current state (a fresh initialisation or
@@ -332,31 +381,11 @@ fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long lon
     hd->stats.cell_solves = (int64_t)c.solves;
     hd->stats.n_bricks = g.nbricks;
     hd->stats.error_flags = c.error;
-    if (T_out) {
-        // host outputs go through the staging buffers (the input the first
-        // one held was consumed by the initialisation, earlier on the stream)
-        const bool host_T = is_host(T_out), host_G = tags_out && is_host(tags_out);
-        void *Td = T_out;
-        uint8_t *Gd = tags_out;
-        if (host_T) {
-            const fmm_status r = stage_buffer(hd, 0, &Td);
-            if (r != FMM_OK)
-                return r;
-        }
-        if (host_G) {
-            if (!hd->stage_tags)
-                FMM_CUDA(hd, alloc(&hd->stage_tags, natural_cells(hd)));
-            Gd = hd->stage_tags;
-        }
-        FMM_CUDA(hd, launch_output(dt, g, s, Td, Gd, st));
-        launches += 1;
-        if (host_T)
-            FMM_CUDA(hd, cudaMemcpyAsync(T_out, Td, natural_cells(hd) * hd->rsize,
-                                         cudaMemcpyDeviceToHost, st));
-        if (host_G)
-            FMM_CUDA(hd, cudaMemcpyAsync(tags_out, Gd, natural_cells(hd), cudaMemcpyDeviceToHost, st));
+    {
+        const fmm_status r = write_outputs(hd, T_out, tags_out, launches);
+        if (r != FMM_OK)
+            return r;
     }
-    FMM_CUDA(hd, cudaStreamSynchronize(st));
     // restarts after the terminating pass only return; the march launches
     // that did work are those of every pass but the last
     const long long worked =
@@ -405,6 +434,96 @@ fmm_status run_restarts(fmm_handle *hd, void *T_out, uint8_t *tags_out, long lon
         return fail(hd, FMM_ERR_TIMEOUT, "a bounded wait of the persistent march gave up");
     if (c.error & ERR_RESTARTS)
         return fail(hd, FMM_ERR_TIMEOUT, "the restart limit was reached before termination");
+    return FMM_OK;
+}
+
+// The cell-parallel march (schedule 4): Algorithm 9, then bucket steps until
+// the step that finds no BAND cell at or below width_band, enqueued in
+// growing batches with the termination flag read between batches (steps
+// enqueued after it return at once); then the output conversion.  The march
+// has no restart boundary to stop on: a solve stopped by max_restarts (here
+// a limit on the bucket steps) or timeout_s cannot be resumed.
+fmm_status run_cell(fmm_handle *hd, void *T_out, uint8_t *tags_out)
+{
+    DeviceState &s = hd->st;
+    const Geom &g = hd->geom;
+    const int dt = hd->cfg.dtype;
+    const SolveParams &p = hd->params;
+    cudaStream_t st = hd->stream;
+    hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
+    const size_t cells = (size_t)g.nbricks * kB3;
+    if (!hd->cell_next)
+        FMM_CUDA(hd, alloc(&hd->cell_next, cells * hd->rsize));
+    if (!hd->cell_min)
+        FMM_CUDA(hd, alloc(&hd->cell_min, 4 * sizeof(unsigned long long)));
+    const bool timing = hd->cfg.time_kernels != 0;
+    while (timing && hd->events.size() < 2) {
+        cudaEvent_t e;
+        FMM_CUDA(hd, cudaEventCreate(&e));
+        hd->events.push_back(e);
+    }
+    FMM_CUDA(hd, launch_reset_control(s, st, p.wait_ns, p.hold));
+    if (timing)
+        FMM_CUDA(hd, cudaEventRecord(hd->events[0], st));
+    FMM_CUDA(hd, launch_cell_begin(dt, g, s, p, hd->cell_next, hd->cell_min, st));
+    long long launches = 4;   // control reset; seed, relax, apply
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit_s = hd->cfg.timeout_s > 0 ? (double)hd->cfg.timeout_s : 600.0;
+    bool timed_out = false, limited = false;
+    long long step = 0, batch = 1;
+    for (;;) {
+        long long n = batch;
+        if (p.max_restarts > 0 && step + n > p.max_restarts)
+            n = p.max_restarts - step;
+        for (long long r = 0; r < n; ++r, ++step) {
+            FMM_CUDA(hd, launch_cell_step(dt, g, s, p, hd->cell_next, hd->cell_min, step, st));
+            launches += 3;
+        }
+        FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA(hd, cudaStreamSynchronize(st));
+        if (hd->h_ctrl->done)
+            break;
+        if (p.max_restarts > 0 && step >= p.max_restarts) {
+            limited = true;
+            break;
+        }
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
+            timed_out = true;
+            break;
+        }
+        if (batch < 64)
+            batch *= 2;
+    }
+    if (timing)
+        FMM_CUDA(hd, cudaEventRecord(hd->events[1], st));
+    const Control c = *hd->h_ctrl;
+    {
+        const fmm_status r = write_outputs(hd, T_out, tags_out, launches);
+        if (r != FMM_OK)
+            return r;
+    }
+    memset(&hd->stats, 0, sizeof(hd->stats));
+    hd->stats.restarts = c.restart;   // bucket steps that accepted cells
+    hd->stats.accepted = (int64_t)c.accepted;
+    hd->stats.cell_solves = (int64_t)c.solves;
+    hd->stats.n_bricks = g.nbricks;
+    hd->stats.error_flags = c.error;
+    hd->stats.kernel_launches = launches + hd->pre_launches;
+    hd->stats.march_launches = 3 * (step + 1);
+    hd->pre_launches = 0;
+    hd->trace.clear();
+    if (timing) {
+        float ms = 0.f;
+        FMM_CUDA(hd, cudaEventElapsedTime(&ms, hd->events[0], hd->events[1]));
+        hd->stats.march_ms = ms;
+    }
+    hd->solved = true;
+    hd->complete = c.done && c.error == 0 && !timed_out && !limited;
+    hd->fwd_ctrl = c;
+    if (timed_out)
+        return fail(hd, FMM_ERR_TIMEOUT, "the solve exceeded its wall-clock limit (timeout_s)");
+    if (limited)
+        return fail(hd, FMM_ERR_TIMEOUT, "the step limit (max_restarts) was reached before termination");
     return FMM_OK;
 }
 
@@ -500,10 +619,20 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
         return fail(nullptr, FMM_ERR_INVALID, "width, stride, bucket and ahead must be >= 0");
     if (cfg->exchange_passes < 0 || cfg->exchange_passes > 64)
         return fail(nullptr, FMM_ERR_INVALID, "exchange_passes must be in [0, 64]");
-    if (cfg->schedule < 0 || cfg->schedule > 3)
-        return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1, 2 or 3");
+    if (cfg->schedule < 0 || cfg->schedule > 4)
+        return fail(nullptr, FMM_ERR_INVALID, "schedule must be 0, 1, 2, 3 or 4");
     if (cfg->deterministic != 0 && cfg->schedule != 0 && cfg->schedule != kSchedulePhased)
         return fail(nullptr, FMM_ERR_INVALID, "deterministic needs the phased schedule (schedule 0 or 1)");
+    if (cfg->accuracy < 0 || cfg->accuracy > 2)
+        return fail(nullptr, FMM_ERR_INVALID, "accuracy must be 0, 1 or 2");
+    if (cfg->accuracy == 2 && cfg->schedule != 0 && cfg->schedule != kScheduleCell)
+        return fail(nullptr, FMM_ERR_INVALID,
+                    "the second-order march runs on the cell-parallel schedule (schedule 0 or 4)");
+    if ((cfg->accuracy == 2 || cfg->schedule == kScheduleCell) && cfg->record_tape)
+        return fail(nullptr, FMM_ERR_INVALID, "the cell-parallel schedule keeps no tape (record_tape must be 0)");
+    if (cfg->accuracy == 2 && cfg->deterministic)
+        return fail(nullptr, FMM_ERR_INVALID, "the second-order march has no deterministic mode (its "
+                                              "results are reproducible without it)");
     if (n_src < 0 || (n_src > 0 && !src_ijk))
         return fail(nullptr, FMM_ERR_INVALID, "bad source list");
     if (speed && !aligned16(speed))
@@ -536,11 +665,13 @@ fmm_status fmm_create(const fmm_config *cfg, const void *speed, double speed_con
                             : cfg->deterministic ? default_stride_deterministic(cfg->dtype)
                                                  : default_stride(cfg->dtype);
     p.stride = stride_h * cfg->h;
-    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;
+    p.bucket = cfg->bucket > 0.0 ? cfg->bucket : cfg->accuracy == 2 ? kSecondOrderBucket : kDefaultBucket;
     p.passes = cfg->exchange_passes > 0 ? cfg->exchange_passes : default_passes(cfg->dtype);
     p.schedule = cfg->schedule == kSchedulePhased || cfg->deterministic ? kSchedulePhased
                  : cfg->schedule == kSchedulePersistent                 ? kSchedulePersistent
+                 : cfg->schedule == kScheduleCell || cfg->accuracy == 2 ? kScheduleCell
                                                                         : kScheduleContinuous;
+    p.accuracy = cfg->accuracy == 2 ? 2 : 1;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();
@@ -644,6 +775,33 @@ fmm_status fmm_reinit_signed_distance(fmm_handle *hd, const void *phi0, void *T_
         return r;
     FMM_CUDA(hd, launch_init_reinit(hd->cfg.dtype, hd->geom, hd->st, hd->params, phi0, hd->stream));
     hd->pre_launches = 1;
+    return run_solve(hd, T_out, tags_out);
+}
+
+fmm_status fmm_solve_fixed(fmm_handle *hd, const void *T0, void *T_out, uint8_t *tags_out)
+{
+    if (!hd)
+        return fail(nullptr, FMM_ERR_INVALID, "handle is NULL");
+    if (!T0 || !aligned16(T0))
+        return fail(hd, FMM_ERR_INVALID, "T0 must be a 16-byte aligned pointer");
+    if (!T_out || !aligned16(T_out))
+        return fail(hd, FMM_ERR_INVALID, "T_out must be a 16-byte aligned pointer");
+    if (hd->n_grids)
+        return fail(hd, FMM_ERR_STATE, "a batch handle solves with fmm_solve_batch");
+    const fmm_status r = device_input(hd, T0, 0, &T0);
+    if (r != FMM_OK)
+        return r;
+    DeviceState &s = hd->st;
+    FMM_CUDA(hd, launch_reset_control(s, hd->stream, hd->params.wait_ns, hd->params.hold));
+    FMM_CUDA(hd, launch_init_fixed(hd->cfg.dtype, hd->geom, s, T0, hd->stream));
+    FMM_CUDA(hd, cudaMemcpyAsync(hd->h_ctrl, s.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, hd->stream));
+    FMM_CUDA(hd, cudaStreamSynchronize(hd->stream));
+    if (hd->h_ctrl->error & ERR_INPUT) {
+        hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
+        return fail(hd, FMM_ERR_INVALID,
+                    "T0 holds a NaN, or a sign change between two cells that are not both finite");
+    }
+    hd->pre_launches = 2;
     return run_solve(hd, T_out, tags_out);
 }
 
@@ -788,6 +946,8 @@ fmm_status fmm_dd_start(fmm_handle *hd, const void *phi0, int64_t extra_lo, int6
         return fail(hd, FMM_ERR_STATE, "batch handles have no domain decomposition");
     if (hd->st.faces)
         return fail(hd, FMM_ERR_STATE, "the fmm_dd_* entry points have no deterministic mode");
+    if (hd->params.schedule == kScheduleCell)
+        return fail(hd, FMM_ERR_STATE, "the fmm_dd_* entry points run the brick march (not schedule 4)");
     if (phi0 && (!aligned16(phi0) || is_host(phi0)))
         return fail(hd, FMM_ERR_INVALID, "phi0 must be 16-byte aligned device memory");
     if (extra_lo < 0 || extra_lo > 1 || extra_hi < 0 || extra_hi > 1)
@@ -1008,6 +1168,9 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
         return fail(nullptr, FMM_ERR_INVALID, "batches keep no tape (record_tape must be 0)");
     if (cfg->deterministic)
         return fail(nullptr, FMM_ERR_INVALID, "batches have no deterministic mode (deterministic must be 0)");
+    if (cfg->schedule == kScheduleCell || cfg->accuracy == 2)
+        return fail(nullptr, FMM_ERR_INVALID,
+                    "batches run the brick schedules (schedule 4 and accuracy 2 are single-grid only)");
     if (cfg->hy != 0.0 || cfg->hz != 0.0)
         return fail(nullptr, FMM_ERR_INVALID, "batches use cubic cells (hy and hz must be 0)");
     std::vector<BatchGrid> grids((size_t)n_grids);
@@ -1071,6 +1234,7 @@ fmm_status fmm_create_batch(int n_grids, const int64_t *dims, const double *h,
     g.nbricks = total;
     SolveParams &p = hd->params;
     set_spacing(p, hmin, 0.0, 0.0);
+    p.accuracy = 1;
     p.width = cfg->width > 0.0 ? cfg->width : INFINITY;
     p.stride = (cfg->stride > 0.0 ? cfg->stride : default_stride(cfg->dtype)) * hmin;
     p.bucket = cfg->bucket > 0.0 ? cfg->bucket : kDefaultBucket;

@@ -39,6 +39,8 @@ enum : int {
     ERR_RESTARTS = 2,     // the restart limit was reached
     ERR_SPEED = 4,        // a speed value was not finite and > 0
     ERR_SPIN = 8,         // a bounded wait of the persistent march gave up
+    ERR_INPUT = 16,       // given interface values: NaN, or a sign change
+                          // without FIX cells at both ends
 };
 
 // Restart control block of Algorithm 16, in device memory.
@@ -111,6 +113,8 @@ struct SolveParams {
     double hy, hz;      // cell sizes along y and z (h on a cubic-cell grid)
     double wy, wz;      // (h/hy)^2, (h/hz)^2: the h_i^2 of Algorithm 11
                         // relative to the x axis
+    int accuracy;       // 1: Eq. (2)-(3); 2: second-order upwind differences
+                        // (the cell-parallel schedule only)
 };
 
 // Cell sizes of Sec. 2.1 (hy, hz <= 0 mean h) and the per-axis weights of
@@ -134,6 +138,7 @@ inline double min_spacing(const SolveParams &p)
 constexpr int kSchedulePhased = 1;
 constexpr int kSchedulePersistent = 2;
 constexpr int kScheduleContinuous = 3;
+constexpr int kScheduleCell = 4;     // cell-parallel bucketed march (fmm_cell.cu)
 constexpr int kMarchWarps = 4;   // bricks in flight per CTA of the march kernels
 #ifndef FMM_RAISE_DIV
 #define FMM_RAISE_DIV 2
@@ -166,6 +171,17 @@ inline int default_passes(int dtype) { return dtype == 1 ? 1 : 2; }
 inline double default_ahead(int) { return INFINITY; }
 inline double default_max_lead() { return INFINITY; }
 constexpr double kDefaultBucket = 4.0;
+// The second-order march's default bucket: a single-axis second-order root
+// exceeds its upwind value by at least (2/3) h / F, so with buckets narrower
+// than 2/3 (units of hmin min(1/F) / sqrt 3) a cell and the neighbour it
+// mainly depends on are not accepted in the same step, and an accepted value
+// is (up to corrections through axes of vanishing weight) final when the
+// cells around it read it, as in the sequential march where every KNOWN
+// value is final.  Wider buckets let a cell accepted with a value that the
+// same step lowers serve as a stale second neighbour, whose too-large psi2
+// lowers the root of another cell below its value; a cell keeps the
+// smallest of its roots, so that error stays.
+constexpr double kSecondOrderBucket = 0.6;
 
 // Device buffers owned by a handle (typed by the launchers).
 struct DeviceState {
@@ -268,6 +284,20 @@ cudaError_t launch_march_to(int dtype, const Geom &g, const DeviceState &s, cons
                             double b0, double b1, cudaStream_t stream);
 cudaError_t launch_minima(int dtype, const Geom &g, const DeviceState &s, cudaStream_t stream);
 cudaError_t launch_reset_list(const DeviceState &s, int which, cudaStream_t stream);
+
+// Cell-parallel march and initialisation from given values (fmm_cell.cu).
+// T0: the caller's x-fastest values (finite: FIX on the side of its sign;
+// +-inf: FAR on that side); sets ERR_INPUT in the control block for NaN or a
+// sign change between two cells that are not both FIX.
+cudaError_t launch_init_fixed(int dtype, const Geom &g, const DeviceState &s, const void *T0,
+                              cudaStream_t stream);
+// next: one value per brick-layout cell (the step's new values); mins: 4
+// words (two slots of the per-side BAND minima).  begin runs Algorithm 9 and
+// fills slot 0; step k accepts from slot k & 1 and fills the other one.
+cudaError_t launch_cell_begin(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
+                              void *next, unsigned long long *mins, cudaStream_t stream);
+cudaError_t launch_cell_step(int dtype, const Geom &g, const DeviceState &s, const SolveParams &p,
+                             void *next, unsigned long long *mins, long long step, cudaStream_t stream);
 
 // Adjoint (fmm_adjoint.cu).  The reverse sweep can run by levels of |psi|
 // of kAdjointLevelStep h each (at most kAdjointMaxLevels); 0 (the default)

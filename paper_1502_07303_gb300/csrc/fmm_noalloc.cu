@@ -133,6 +133,8 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
         return error(FMM_ERR_INVALID, "the no-allocation entry point keeps no tape (record_tape must be 0)");
     if (cfg->deterministic)
         return error(FMM_ERR_INVALID, "the no-allocation entry point has no deterministic mode");
+    if (cfg->accuracy != 0 && cfg->accuracy != 1)
+        return error(FMM_ERR_INVALID, "the no-allocation entry point runs the first-order march (accuracy 0 or 1)");
     if (!phi0 || ((uintptr_t)phi0 & 15u) || !T_out || ((uintptr_t)T_out & 15u))
         return error(FMM_ERR_INVALID, "phi0 and T_out must be 16-byte aligned device pointers");
     Geom g;
@@ -190,6 +192,7 @@ extern "C" fmm_status fmm_reinit_signed_distance_noalloc(const fmm_config *cfg, 
     p.schedule = cfg->schedule == kSchedulePhased      ? kSchedulePhased
                  : cfg->schedule == kSchedulePersistent ? kSchedulePersistent
                                                         : kScheduleContinuous;
+    p.accuracy = 1;
     p.max_restarts = cfg->max_restarts > 0 ? cfg->max_restarts : 0;
     p.max_rounds = 1 << 22;
     p.max_lead = cfg->max_lead > 0 ? (double)cfg->max_lead : default_max_lead();

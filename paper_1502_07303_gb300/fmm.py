@@ -27,7 +27,7 @@ EXPORTED = ("fmm_create", "fmm_set_speed", "fmm_solve", "fmm_reinit_signed_dista
             "fmm_checkpoint_load", "fmm_selftest_fp64", "fmm_selftest_root", "fmm_probe_fma_rate",
             "fmm_solve_batch",
             "fmm_dd_start", "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers",
-            "fmm_dd_integrate", "fmm_dd_finish")
+            "fmm_dd_integrate", "fmm_dd_finish", "fmm_solve_fixed")
 
 
 class FmmConfig(ctypes.Structure):
@@ -41,7 +41,7 @@ class FmmConfig(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("max_lead", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("hold_queue", ctypes.c_int32),
                 ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("ahead", ctypes.c_double),
-                ("deterministic", ctypes.c_int32)]
+                ("deterministic", ctypes.c_int32), ("accuracy", ctypes.c_int32)]
 
 
 class FmmStats(ctypes.Structure):
@@ -89,6 +89,7 @@ def load(path: str | None = None):
     lib.fmm_create.argtypes = [ctypes.POINTER(FmmConfig), vp, dbl, vp, i64, ctypes.POINTER(vp)]
     lib.fmm_set_speed.argtypes = [vp, vp, dbl]
     lib.fmm_solve.argtypes = [vp, vp, vp]
+    lib.fmm_solve_fixed.argtypes = [vp, vp, vp, vp]
     lib.fmm_reinit_signed_distance.argtypes = [vp, vp, vp, vp]
     lib.fmm_adjoint.argtypes = [vp, vp, vp]
     lib.fmm_get_stats.argtypes = [vp, ctypes.POINTER(FmmStats)]
@@ -122,7 +123,7 @@ def load(path: str | None = None):
               "fmm_selftest_fp64", "fmm_selftest_root", "fmm_probe_fma_rate", "fmm_solve_batch",
               "fmm_dd_start",
               "fmm_dd_minima", "fmm_dd_march", "fmm_dd_get_layers", "fmm_dd_integrate",
-              "fmm_dd_finish"):
+              "fmm_dd_finish", "fmm_solve_fixed"):
         getattr(lib, n).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -168,21 +169,22 @@ class Solver:
     """One handle of the CUDA library: a grid (nz, ny, nx), cell size h (one
     value, or (dx, dy, dz) for cells of unequal sides), dtype, a speed field
     (tensor on the device or a constant) and optional point sources
-    (i, j, k)."""
+    (i, j, k).  accuracy=2 selects the second-order march (on the
+    cell-parallel schedule 4)."""
 
     def __init__(self, shape, h, dtype=torch.float32, speed=None, sources=None,
                  width=math.inf, stride=0.0, bucket=0.0, record_tape=False, ctas=0,
                  max_restarts=0, timeout_s=0, time_kernels=False, exchange_passes=0,
                  schedule=0, max_lead=0, wait_limit_ms=0, hold_queue=0, ahead=0.0, stream=None,
-                 tuned=True, deterministic=False):
+                 tuned=True, deterministic=False, accuracy=1):
         self.lib = load()
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.code, self.dtype = _dtype_code(dtype)
         self.stream = stream
-        if deterministic:
-            # the phased schedule with pass-synchronous halos; the tuned
-            # schedules do not apply
+        if deterministic or accuracy == 2 or schedule == 4:
+            # the phased schedule with pass-synchronous halos, or the
+            # cell-parallel march: the tuned schedules do not apply
             tuned = False
         if tuned:
             # parameters left at 0 take the autotuner's cached values (if any)
@@ -215,6 +217,7 @@ class Solver:
         cfg.hold_queue = int(hold_queue)
         cfg.ahead = float(ahead)
         cfg.deterministic = 1 if deterministic else 0
+        cfg.accuracy = int(accuracy)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         sp_ptr, sp_const = self._speed_args(speed)
@@ -261,6 +264,14 @@ class Solver:
     def solve(self, T_out=None, tags_out=None, want_tags=True):
         T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags)
         self._check(self.lib.fmm_solve(self.handle, tp, gp))
+        return T_out, tags_out
+
+    def solve_fixed(self, T0, T_out=None, tags_out=None, want_tags=True):
+        """Solve from given interface values: finite entries of T0 are FIX
+        cells (side of their sign), +-inf FAR cells of that side."""
+        pp = _dev_ptr(T0, self.dtype, self.shape, "T0", host_ok=True)
+        T_out, tags_out, tp, gp = self._outputs(T_out, tags_out, want_tags, T0.device)
+        self._check(self.lib.fmm_solve_fixed(self.handle, pp, tp, gp))
         return T_out, tags_out
 
     def reinit(self, phi0, T_out=None, tags_out=None, want_tags=True):

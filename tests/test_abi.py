@@ -148,3 +148,46 @@ def test_deterministic_mode_needs_the_phased_schedule():
         rc = lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h))
         assert rc == fmm.FMM_ERR_INVALID and not h.value
         assert b"deterministic" in lib.fmm_last_error(None)
+
+
+def test_second_order_and_cell_schedule_argument_checks():
+    """fmm_create refuses the second-order march off the cell-parallel
+    schedule, with a tape or in deterministic mode, an accuracy outside
+    0..2 and a schedule above 4; fmm_create_batch refuses schedule 4 and
+    accuracy 2 (argument checks run before any CUDA call: no GPU needed)."""
+    from paper_1502_07303_gb300 import fmm
+    lib = fmm.load()
+
+    def cfg_of(**kw):
+        cfg = fmm.FmmConfig()
+        cfg.nx = cfg.ny = cfg.nz = 8
+        cfg.h = 0.125
+        cfg.dtype = 1
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        return cfg
+
+    cases = [
+        (dict(accuracy=2, schedule=1), b"cell-parallel"),
+        (dict(accuracy=2, schedule=3), b"cell-parallel"),
+        (dict(accuracy=2, record_tape=1), b"tape"),
+        (dict(schedule=4, record_tape=1), b"tape"),
+        (dict(accuracy=2, deterministic=1), b"deterministic"),
+        (dict(accuracy=3), b"accuracy"),
+        (dict(accuracy=-1), b"accuracy"),
+        (dict(schedule=5), b"schedule"),
+    ]
+    for kw, word in cases:
+        cfg = cfg_of(**kw)
+        h = ctypes.c_void_p()
+        rc = lib.fmm_create(ctypes.byref(cfg), None, 1.0, None, 0, ctypes.byref(h))
+        assert rc == fmm.FMM_ERR_INVALID and not h.value, kw
+        assert word in lib.fmm_last_error(None), (kw, lib.fmm_last_error(None))
+    dims = (ctypes.c_int64 * 3)(8, 8, 8)
+    hs = (ctypes.c_double * 1)(0.125)
+    for kw in (dict(schedule=4), dict(accuracy=2)):
+        cfg = cfg_of(**kw)
+        h = ctypes.c_void_p()
+        rc = lib.fmm_create_batch(1, dims, hs, ctypes.byref(cfg), ctypes.byref(h))
+        assert rc == fmm.FMM_ERR_INVALID and not h.value, kw
+        assert b"single-grid" in lib.fmm_last_error(None)

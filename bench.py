@@ -387,6 +387,55 @@ def measure_e2e(fmm, torch, phi_host, p, dtype, steps, warmup, stream, params):
     return statistics.mean(times), nbytes, T_host.numel() * T_host.element_size()
 
 
+# bytes one bucket step of the cell-parallel march streams per cell (brick
+# layout, fp64): accept reads psi + tag (9), relax reads psi + tag (9; the
+# neighbours' values come from L1/L2), apply reads psi + tag + the new-value
+# buffer (17)
+CELL_STEP_BYTES = {"f64": 35, "f32": 19}
+
+
+def measure_second_order(fmm, torch, wl, stream, flush, n=256, steps=3, warmup=2):
+    """The cell-parallel march (schedule 4) in first and second order on the
+    single-sphere reinitialisation (fp64), with the error of each against
+    the exact signed distance (phi0 is exact for one sphere), and the brick
+    march (first order, library defaults) on the same workload for scale.
+    Roofline: the bytes the march's grid-wide passes stream per bucket step
+    (CELL_STEP_BYTES per brick-layout cell) over the device time of the
+    march, against the measured copy peak."""
+    p = wl.single_sphere(n=n, radius=RADIUS, device="cuda")
+    phi = p.phi0.contiguous()
+    exact = phi.abs()
+    out = {"workload": f"reinit single sphere r={RADIUS} centred, {n}^3, fp64", "points": p.n_points}
+    cells = ((n + 7) // 8) ** 3 * 512
+    peak, peak_kind = peaks()
+    for name, prm in (("brick_first_order", {}), ("cell_first_order", {"schedule": 4}),
+                      ("cell_second_order", {"schedule": 4, "accuracy": 2})):
+        r = measure(fmm, torch, p, torch.float64, steps, warmup, flush, stream, prm, phi=phi)
+        with fmm.Solver(p.shape, p.h, dtype=torch.float64, stream=stream, tuned=False, **prm) as s:
+            T, _ = s.reinit(phi)
+        err = (T.abs() - exact).abs()
+        rec = {"ms": r["ms"], "gpts": p.n_points / r["ms"] / 1e6, "params": prm,
+               "err_max": float(err.max()), "err_mean": float(err.mean()),
+               "accepted_per_point": r["stats"]["accepted"] / p.n_points}
+        if prm.get("schedule") == 4:
+            # bucket steps that accepted cells, plus the one that ended the
+            # march (steps enqueued after it return at once)
+            nsteps = r["stats"]["restarts"] + 1
+            achieved = CELL_STEP_BYTES["f64"] * cells * nsteps / (r["march_ms"] / 1e3) / 1e9
+            rec["bucket_steps"] = nsteps
+            rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": achieved / peak, "peak_kind": peak_kind,
+                               "bytes_per_cell_per_step": CELL_STEP_BYTES["f64"],
+                               "kernels": "k_cell_accept + k_cell_relax + k_cell_apply",
+                               "march_ms": r["march_ms"], "share_of_step": r["march_ms"] / r["ms"]}
+        out[name] = rec
+        del T, err
+    out["second_vs_first_order_err_mean"] = out["cell_first_order"]["err_mean"] / out["cell_second_order"]["err_mean"]
+    del p, phi, exact
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_adjoint(fmm, torch, wl, stream, n=512, steps=2, warmup=1, dtypes=("f32", "f64"),
                     params=None):
     """Heterogeneous speed F = exp(g/2) (16 random Fourier modes), 8 point
@@ -564,6 +613,14 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     DTS = {"f32": torch.float32, "f64": torch.float64}
 
+    if args.part == "so":
+        # only the second-order / cell-parallel measurement (for profiling)
+        r = measure_second_order(fmm, torch, wl, stream, flush, n=args.n or 256, steps=args.steps,
+                                 warmup=args.warmup)
+        if rank == 0:
+            print(json.dumps({"part": args.part, **r}), flush=True)
+        return 0
+
     if args.part in ("c2-f32", "c2-f64", "c5-f32", "c5-f64"):
         # one timed solve series of one workload and dtype (for profiling)
         w, name = args.part.split("-")
@@ -664,6 +721,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         others["adjoint"] = measure_adjoint(fmm, torch, wl, stream, params=adj_params)
         others["batched"] = measure_batch(fmm, torch, wl, autotune, stream)
+        others["second_order"] = measure_second_order(fmm, torch, wl, stream, flush,
+                                                      steps=min(args.steps, 3), warmup=1)
 
     if rank != 0:
         return 0
@@ -750,9 +809,11 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="only the headline workload (fp64 and fp32), no other configs")
     ap.add_argument("--part", default="all",
-                    choices=["all", "c2-f32", "c2-f64", "c5-f32", "c5-f64", "adjoint-f32", "adjoint-f64"],
+                    choices=["all", "c2-f32", "c2-f64", "c5-f32", "c5-f64", "adjoint-f32", "adjoint-f64",
+                             "so"],
                     help="c2-* / c5-*: only the timed solves of one workload and dtype; "
-                         "adjoint-*: only the forward + adjoint pair (for profiling)")
+                         "adjoint-*: only the forward + adjoint pair; so: only the cell-parallel "
+                         "march in first and second order (for profiling)")
     ap.add_argument("--adjoint-n", type=int, default=512,
                     help="grid size of the adjoint workload of --part adjoint-*")
     ap.add_argument("--params", type=_params, default=None,

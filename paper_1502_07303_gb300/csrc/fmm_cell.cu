@@ -63,15 +63,32 @@ __device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
 
 __device__ __forceinline__ bool known(uint8_t t) { return (t & ST_MASK) >= ST_KNOWN; }
 
-// Natural coordinates of brick-layout cell e.
+// a < b and a <= b for values >= 0 (+inf included) on their bit patterns:
+// integer compares, off the FP64 pipe that runs at 1/64 of the float rate
+__device__ __forceinline__ bool blt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool blt(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+__device__ __forceinline__ bool ble(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+__device__ __forceinline__ bool ble(float a, float b) { return __float_as_int(a) <= __float_as_int(b); }
+// |v| with the sign bit cleared (-0 becomes +0, which the compares above
+// need)
+__device__ __forceinline__ double abs_bits(double v) { return __longlong_as_double(__double_as_longlong(v) & 0x7fffffffffffffffll); }
+__device__ __forceinline__ float abs_bits(float v) { return __int_as_float(__float_as_int(v) & 0x7fffffff); }
+// the "no new value" mark (all bits set)
+__device__ __forceinline__ bool is_none(double v) { return __double_as_longlong(v) == -1ll; }
+__device__ __forceinline__ bool is_none(float v) { return __float_as_int(v) == -1; }
+
+// Natural coordinates of brick-layout cell e (32-bit divisions: the brick
+// count of a grid of at most 2^20 cells per axis that fits in memory is far
+// below 2^32).
 __device__ __forceinline__ void cell_ijk(const Geom &g, long long e, int &i, int &j, int &k)
 {
-    const long long b = e >> 9;
+    const unsigned b = (unsigned)(e >> 9);
     const int c = (int)(e & 511);
-    const int bx = (int)(b % g.nbx);
-    const long long r = b / g.nbx;
-    const int by = (int)(r % g.nby);
-    const int bz = (int)(r / g.nby);
+    const unsigned nbx = (unsigned)g.nbx, nby = (unsigned)g.nby;
+    const int bx = (int)(b % nbx);
+    const unsigned r = b / nbx;
+    const int by = (int)(r % nby);
+    const int bz = (int)(r / nby);
     i = bx * kB + (c & 7);
     j = by * kB + ((c >> 3) & 7);
     k = bz * kB + (c >> 6);
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(kCellThreads) k_init_fixed(Geom g, const real 
             continue;
         }
         const bool fixed = v > -inf_r<real>() && v < inf_r<real>();
-        T[e] = fixed ? (neg ? -v : v) : inf_r<real>();
+        T[e] = fixed ? abs_bits(v) : inf_r<real>();
         tag[e] = (uint8_t)((fixed ? ST_FIX : ST_FAR) | (neg ? TG_NEG : 0));
         if (!fixed) {
             const int c[3] = {i, j, k};
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_relax(Geom g, const real 
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             nb[q] = cell_along(g, i, j, k, q >> 1, (q & 1) ? 1 : -1);
-            if (nb[q] >= 0 && (tag[nb[q]] & TG_ACC) && T[nb[q]] < Tc)
+            if (nb[q] >= 0 && (tag[nb[q]] & TG_ACC) && blt(T[nb[q]], Tc))
                 trig = true;
         }
         if (!trig)
@@ -302,12 +319,12 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_relax(Geom g, const real 
             const bool km = qm >= 0 && known(tag[qm]), kp = qp >= 0 && known(tag[qp]);
             const real vm = km ? T[qm] : inf_r<real>(), vp = kp ? T[qp] : inf_r<real>();
             int d = 0;
-            if (km && vm < Tc)
+            if (km && blt(vm, Tc))
                 d = -1;
-            if (kp && vp < Tc) {
+            if (kp && blt(vp, Tc)) {
                 if (d == 0)
                     d = 1;
-                else if (vp < vm)
+                else if (blt(vp, vm))
                     d = 1;
             }
             if (d == 0)
@@ -319,7 +336,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_relax(Geom g, const real 
                 const long long q2 = cell_along(g, i, j, k, a, 2 * d);
                 if (q2 >= 0 && known(tag[q2])) {
                     const real v2 = T[q2];
-                    if (v2 <= psi[a]) {
+                    if (ble(v2, psi[a])) {
                         psi[a] = ((real)4 * psi[a] - v2) / (real)3;
                         W[a] = W[a] * (real)2.25;
                     }
@@ -328,7 +345,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_relax(Geom g, const real 
         }
         const real q = spd ? spd[e] : (real)spd_const;
         const real r = cell_root<real>(psi, W, act, q);
-        if (r < Tc)
+        if (blt(r, Tc))
             next[e] = r;
     }
     solves = __reduce_add_sync(FULL, solves);
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_apply(Geom g, real *T, ui
         uint8_t nt = (uint8_t)(t & ~TG_ACC);
         real v = T[e];
         const real nv = next[e];
-        if (nv == nv) {
+        if (!is_none(nv)) {
             v = nv;
             T[e] = nv;
             next[e] = none_r<real>();
@@ -364,21 +381,21 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_apply(Geom g, real *T, ui
             tag[e] = nt;
         if ((nt & ST_MASK) == ST_BAND) {
             if (nt & TG_NEG)
-                l0 = v < l0 ? v : l0;
+                l0 = blt(v, l0) ? v : l0;
             else
-                l1 = v < l1 ? v : l1;
+                l1 = blt(v, l1) ? v : l1;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const real a = __shfl_xor_sync(FULL, l0, o), b = __shfl_xor_sync(FULL, l1, o);
-        l0 = a < l0 ? a : l0;
-        l1 = b < l1 ? b : l1;
+        l0 = blt(a, l0) ? a : l0;
+        l1 = blt(b, l1) ? b : l1;
     }
     if ((threadIdx.x & 31) == 0) {
-        if (l0 < inf_r<real>())
+        if (blt(l0, inf_r<real>()))
             atomicMin(&mins[2 * slot], (unsigned long long)__double_as_longlong((double)l0));
-        if (l1 < inf_r<real>())
+        if (blt(l1, inf_r<real>()))
             atomicMin(&mins[2 * slot + 1], (unsigned long long)__double_as_longlong((double)l1));
     }
 }

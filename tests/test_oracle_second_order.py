@@ -263,3 +263,83 @@ def test_second_order_result_depends_on_the_update_order(oracle):
         assert np.abs(lc2 - seq2).max() > 1e-4
         err_seq, err_lc = np.abs(seq2 - R).max(), np.abs(lc2 - R).max()
         assert err_lc < 1.5 * err_seq
+
+
+def _jacobi_bucket_march(oracle, T0, G0, h3, F, bucket):
+    """Second-order bucket steps in the order of updates of the GPU's
+    cell-parallel schedule, written with the oracle's local solve: each step
+    accepts the BAND cells within bucket * (hmin / (sqrt 3 max F of the 8^3
+    brick)) of the band minimum, solves every non-FIX cell above a neighbour
+    accepted in the step from the state before the step, then applies the
+    improvements (an improved cell is BAND again)."""
+    T = T0.copy()
+    fix = G0 == oracle.KNOWN_FIX
+    known = fix.copy()
+    shape = T.shape
+    bd = np.empty(shape)
+    for bz in range(0, shape[0], 8):
+        for by in range(0, shape[1], 8):
+            for bx in range(0, shape[2], 8):
+                sl = (slice(bz, bz + 8), slice(by, by + 8), slice(bx, bx + 8))
+                bd[sl] = min(h3) / (math.sqrt(3.0) * F[sl].max())
+    steps = [(0, 0, 1), (0, 1, 0), (1, 0, 0)]
+
+    def inside(q):
+        return all(0 <= q[a] < shape[a] for a in range(3))
+
+    def solve(p):
+        nb, kn = np.full(6, np.inf), np.zeros(6, np.uint8)
+        nb2, kn2 = np.zeros(6), np.zeros(6, np.uint8)
+        for ax, d in enumerate(steps):
+            for si, s in enumerate((-1, 1)):
+                q = tuple(p[a] + s * d[a] for a in range(3))
+                q2 = tuple(p[a] + 2 * s * d[a] for a in range(3))
+                if inside(q):
+                    nb[2 * ax + si], kn[2 * ax + si] = T[q], known[q]
+                if inside(q2):
+                    nb2[2 * ax + si], kn2[2 * ax + si] = T[q2], known[q2]
+        return oracle.local_solve(nb, kn, T[p], h3, F[p], nb2=nb2, nb2_known=kn2)
+
+    def step(acc):
+        new = {}
+        for p in zip(*np.nonzero(~fix)):
+            hit = False
+            for d in steps:
+                for s in (-1, 1):
+                    q = tuple(p[a] + s * d[a] for a in range(3))
+                    hit = hit or (inside(q) and acc[q] and T[q] < T[p])
+            if hit:
+                t = solve(p)
+                if t < T[p]:
+                    new[p] = t
+        for p, t in new.items():
+            T[p] = t
+            known[p] = False
+
+    step(fix.copy())
+    while True:
+        band = ~known & np.isfinite(T)
+        if not band.any():
+            return T
+        acc = band & (T <= T[band].min() + bucket * bd)
+        known |= acc
+        step(acc)
+
+
+def test_second_order_bucket_steps_need_narrow_buckets(oracle):
+    """With the GPU's update order (Jacobi bucket steps), a cell accepted
+    with a value the same step lowers can serve as a too-large second
+    neighbour and pull another cell's root below the exact value for good;
+    buckets below the smallest single-axis increment (2/3) keep the
+    quadratic bowl exact, wide ones (4, the first-order default) do not."""
+    n = 16
+    h3 = (1 / 16, 1.5 / 16, 0.75 / 16)
+    coords = [(np.arange(n) + 1.0) * h for h in h3]
+    Z, Y, X = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+    T_ex = 0.5 * (X * X + Y * Y + Z * Z)
+    F = 1.0 / np.sqrt(X * X + Y * Y + Z * Z)
+    T0, G0 = _fix(T_ex, np.indices((n, n, n)).min(axis=0) < 2, oracle)
+    narrow = _jacobi_bucket_march(oracle, T0, G0, h3, F, 0.6)
+    wide = _jacobi_bucket_march(oracle, T0, G0, h3, F, 4.0)
+    assert np.abs(narrow - T_ex).max() / T_ex.max() <= 1e-13
+    assert np.abs(wide - T_ex).max() / T_ex.max() > 1e-9

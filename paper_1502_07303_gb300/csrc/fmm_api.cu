@@ -451,6 +451,8 @@ fmm_status run_cell(fmm_handle *hd, void *T_out, uint8_t *tags_out)
     const SolveParams &p = hd->params;
     cudaStream_t st = hd->stream;
     hd->solved = hd->tape_valid = hd->resumable = hd->complete = false;
+    if (g.nbricks > 0xffffffffll)
+        return fail(hd, FMM_ERR_INVALID, "the cell-parallel schedule takes grids of fewer than 2^32 bricks");
     const size_t cells = (size_t)g.nbricks * kB3;
     if (!hd->cell_next)
         FMM_CUDA(hd, alloc(&hd->cell_next, cells * hd->rsize));

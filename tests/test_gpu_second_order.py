@@ -13,8 +13,6 @@ solve from given interface values, against the oracle.
   the GPU's error against the exact distance falls by about 4 per halving
   of h and stays within a small factor of the oracle's
 """
-import math
-
 import numpy as np
 import pytest
 import torch

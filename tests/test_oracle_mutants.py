@@ -20,6 +20,10 @@ _spec2 = importlib.util.spec_from_file_location(
     "oracle_second_order", os.path.join(_HERE, "test_oracle_second_order.py"))
 so = importlib.util.module_from_spec(_spec2)
 _spec2.loader.exec_module(so)
+_spec3 = importlib.util.spec_from_file_location(
+    "oracle_golden", os.path.join(_HERE, "test_golden.py"))
+golden = importlib.util.module_from_spec(_spec3)
+_spec3.loader.exec_module(golden)
 
 MUTANTS = {
     "discriminant_sign": ("double disc = qb * qb - (4.0 * qa) * qc;",
@@ -66,6 +70,7 @@ MUTANTS = {
 }
 
 PINS = [
+    (golden.test_sec2_2_upwind_examples, {}),
     (pins.test_closed_forms_unit_speed, {}),
     (pins.test_closed_forms_scaled, {}),
     (pins.test_local_solve_cases, {}),

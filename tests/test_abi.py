@@ -59,6 +59,7 @@ def test_create_error_without_gpu_is_reported():
     assert lib.fmm_create(ctypes.byref(cfg), None, 1.0, src, 1, ctypes.byref(h)) == fmm.FMM_ERR_INVALID
     assert b"outside" in lib.fmm_last_error(None)
     assert lib.fmm_solve(None, None, None) == fmm.FMM_ERR_INVALID
+    assert lib.fmm_solve_fixed(None, None, None, None) == fmm.FMM_ERR_INVALID
     lib.fmm_destroy(None)
 
 
